@@ -1,0 +1,149 @@
+"""Pins of the oracle's estimator (Sec. 2.2) to brute force, closed forms and invariants. CPU only."""
+import numpy as np
+import pytest
+
+import fieldgen
+from oracle import analytic as A
+from oracle import dbe
+from oracle import fbe
+from oracle import plan as P
+
+
+def _plan(ng, ns=8, top=None, **kw):
+    return P.make_plan(ng, float(ng), P.linear_edges(ns, 1.0, top or ng / 4), **kw)
+
+
+@pytest.mark.parametrize("ng,seed", [(16, 2), (32, 1)])
+def test_fbe_equals_direct_summation(ng, seed):
+    """Eq. (2.7)/(2.10) through FFTs equal Eq. (2.3)/(2.9) summed mode by mode."""
+    pl = _plan(ng)
+    spec = fieldgen.spectrum(fieldgen.quadratic_field(ng, float(ng), 2.0, 0.1, seed))
+    res = fbe.estimate(spec, pl)
+    msum_d, ntri_d = dbe.direct_estimate(spec, pl)
+    assert set(ntri_d) == set(res["triplets"])
+    ng3 = float(ng) ** 3
+    for i, t in enumerate(res["triplets"]):
+        assert ntri_d[t] == res["ntri"][i]
+        m = msum_d[t]
+        assert abs(m.imag) <= 1e-12 * abs(m.real) + 1e-9
+        assert abs(res["msum"][i] / ng3 - m.real) <= 1e-12 * abs(m.real)
+
+
+def test_triangle_counts_alias_above_cap():
+    """Fig. 4: above k = 2 pi Ng/(3L) the FFT count exceeds the direct count; below it agrees."""
+    ng = 16
+    pl = _plan(ng, ns=6, top=7.0, allow_aliasing=True)
+    tsum, ntri = fbe.triangle_counts(pl)
+    _, ntri_d = dbe.direct_estimate(None, pl, count_only=True)
+    over = 0
+    for t, n in zip(pl.candidates, np.rint(ntri).astype(int)):
+        nd = ntri_d.get(t, 0)
+        kmax = np.sqrt(pl.thresholds[t[0] + 1] - 1)
+        if 3 * kmax < ng:
+            assert n == nd
+        else:
+            assert n >= nd
+            over += n > nd
+    assert over > 0
+
+
+def test_closed_form_three_cosines():
+    """delta = 2A [cos(k1.x) + cos(k2.x) + cos(k3.x)] with k1 + k2 + k3 = 0 in three shells:
+    sum_x d_a d_b d_c = 8 A^3 Ng^9 sum_x cos cos cos = 2 A^3 Ng^12 (all other products vanish)."""
+    ng, amp = 32, 0.7
+    pl = _plan(ng)
+    m1, m2 = np.array([6, 1, 2]), np.array([-2, -3, 1])
+    m3 = -(m1 + m2)
+    x = np.indices((ng, ng, ng)).reshape(3, -1).T
+    delta = sum(2 * amp * np.cos(2 * np.pi * (x @ m) / ng) for m in (m1, m2, m3)).reshape(ng, ng, ng)
+    sh = [int(np.searchsorted(pl.thresholds, (m * m).sum(), side="right") - 1) for m in (m1, m2, m3)]
+    a, b, c = sorted(sh, reverse=True)
+    assert a > b > c
+    res = fbe.estimate(fieldgen.spectrum(delta), pl)
+    i = res["triplets"].index((a, b, c))
+    assert abs(res["msum"][i] - 2 * amp ** 3 * float(ng) ** 12) <= 1e-10 * 2 * amp ** 3 * float(ng) ** 12
+    others = [abs(v) for j, v in enumerate(res["msum"]) if j != i]
+    assert max(others) <= 1e-9 * float(ng) ** 12
+
+
+def test_invariants():
+    """Translation, the cube symmetries, delta -> alpha delta (alpha^3) and delta -> -delta."""
+    ng = 16
+    pl = _plan(ng)
+    d = fieldgen.quadratic_field(ng, float(ng), 2.0, 0.3, 5)
+    counts = fbe.kept_triplets(pl)
+    b0 = fbe.estimate(fieldgen.spectrum(d), pl, counts=counts)["b"]
+    scale = np.abs(b0).max()
+
+    def b(x):
+        return fbe.estimate(fieldgen.spectrum(x), pl, counts=counts)["b"]
+
+    assert np.abs(b(np.roll(d, (3, -5, 7), axis=(0, 1, 2))) - b0).max() <= 1e-12 * scale
+    assert np.abs(b(np.transpose(d, (2, 0, 1))) - b0).max() <= 1e-12 * scale
+    assert np.abs(b(d[::-1, :, ::-1]) - b0).max() <= 1e-12 * scale
+    assert np.abs(b(2.5 * d) - 2.5 ** 3 * b0).max() <= 1e-12 * 2.5 ** 3 * scale
+    assert np.abs(b(-d) + b0).max() <= 1e-12 * scale
+
+
+def test_parseval_shell_power():
+    """sum_x d_n^2 = Ng^3 sum_{k in n} |F(k)|^2 over the full grid (Parseval)."""
+    ng = 32
+    pl = _plan(ng)
+    d = fieldgen.quadratic_field(ng, float(ng), 1.5, 0.1, 9)
+    spec = fieldgen.spectrum(d)
+    fields = fbe.shell_fields(spec, pl)
+    full = np.fft.fftn(d)
+    m = np.fft.fftfreq(ng, 1.0 / ng)
+    q = m[:, None, None] ** 2 + m[None, :, None] ** 2 + m[None, None, :] ** 2
+    for n in range(pl.ns):
+        sel = (q >= pl.thresholds[n]) & (q < pl.thresholds[n + 1])
+        lhs = float(np.sum(fields[n] ** 2))
+        rhs = float(ng) ** 3 * float(np.sum(np.abs(full[sel]) ** 2))
+        assert abs(lhs - rhs) <= 1e-12 * rhs
+
+
+@pytest.mark.parametrize("beta", [None, 0.5])
+def test_ensemble_mean_matches_expected_bispectrum(beta):
+    """Mean over 100 realisations of the quadratic field (Eq. (3.1), f_NG = 0.5 as in Sec. 3)
+    against Eq. (2.5) with Eq. (3.2) summed over the grid triangles (with Eq. (3.4) factors for
+    RSD); chi^2 per bin about 1. A 30 percent error gives chi^2/dof ~ 10, a sign error ~ 500."""
+    ng, f = 32, 0.5
+    pl = _plan(ng)
+    counts = fbe.kept_triplets(pl)
+    exp = A.expected_binned(pl, counts[0], 2.0, f, beta=beta)
+    bs = np.array([fbe.estimate(fieldgen.spectrum(fieldgen.quadratic_field(ng, float(ng), 2.0, f, 1000 + s)),
+                                pl, beta=beta, counts=counts)["b"] for s in range(100)])
+    z = (bs.mean(0) - exp) / (bs.std(0, ddof=1) / np.sqrt(len(bs)))
+    assert np.mean(z ** 2) < 2.0
+    assert np.mean(np.abs(z) > 4) < 0.02
+
+
+def test_gaussian_field_has_zero_mean_bispectrum():
+    ng = 32
+    pl = _plan(ng)
+    counts = fbe.kept_triplets(pl)
+    bs = np.array([fbe.estimate(fieldgen.spectrum(fieldgen.gaussian_field(ng, float(ng), 2.0, 50 + s)),
+                                pl, counts=counts)["b"] for s in range(60)])
+    z = bs.mean(0) / (bs.std(0, ddof=1) / np.sqrt(len(bs)))
+    assert np.mean(z ** 2) < 2.0
+
+
+def test_expected_binned_tends_to_eq_3_2_at_shell_means():
+    """For bins far from the squeezed and linear limits, the grid-summed expectation is close
+    to Eq. (3.2) evaluated at the shell means (finite-width effects of a few percent)."""
+    ng, f = 64, 0.5
+    pl = _plan(ng, ns=8)
+    trips = [(7, 7, 7), (7, 6, 5), (6, 6, 6), (7, 7, 6)]
+    exp = A.expected_binned(pl, trips, 2.0, f)
+    for (a, b, c), e in zip(trips, exp):
+        p = A.power_law(pl.kf * pl.kbar[[a, b, c]], 2.0)
+        ana = A.b_ana(p[0], p[1], p[2], f)
+        assert abs(e - ana) <= 0.05 * ana
+
+
+def test_condition_scale_bounds_the_sum():
+    ng = 16
+    pl = _plan(ng)
+    spec = fieldgen.spectrum(fieldgen.quadratic_field(ng, float(ng), 2.0, 0.1, 3))
+    res = fbe.estimate(spec, pl, with_abs=True)
+    assert np.all(np.abs(res["msum"]) <= res["asum"] * (1 + 1e-12))
