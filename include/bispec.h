@@ -1,0 +1,150 @@
+/*
+ * bispec.h - C ABI of the GB300 (sm_103a) FFT bin-averaged 3D bispectrum estimator.
+ *
+ * The estimator is the fast bispectrum estimator (FBE) of Shaw et al., "A fast estimator
+ * for quantifying the shape dependence of the 3D bispectrum" (arXiv:2107.14564), Sec. 2:
+ *
+ *   B(a,b,c) = V_c^3 sum_x d_a(x) d_b(x) d_c(x) / (V sum_x i_a(x) i_b(x) i_c(x))
+ *
+ * Eq. (2.7) with Eq. (2.10) (Ng^3 cancels), where for every spherical k shell n
+ *   d_n(x) = sum_{k in n} F(k) e^{+i k.x}   (Eq. (2.8); D(k_n,x) = V_c d_n(-x))
+ *   i_n(x) = sum_{k in n}      e^{+i k.x}   (Eq. (2.11))
+ * and F(k) = sum_x delta(x) e^{-i k.x} is the unnormalised DFT of the density field
+ * (Delta(k) = V_c F(k) is the Fourier transform of Eq. (2.1); V = L^3, V_c = (L/Ng)^3).
+ * Bins are the shell triplets a >= b >= c with at least one closed triangle (Sec. 2.1),
+ * labelled by (k1, mu, t) of Eq. (2.4).
+ *
+ * Conventions shared by every entry point
+ *  - Grids are C-order [x][y][z]; z is the last axis, the axis the real FFT halves and the
+ *    line of sight of the optional linear RSD factor (Eq. (3.4)).
+ *  - A half spectrum is [Ng][Ng][Ng/2+1] interleaved complex (re, im): complex128 for
+ *    BSP_FP64 plans, complex64 for BSP_FP32 and BSP_MIXED_BF16X3 plans. Index (i, j, l)
+ *    holds the mode m = (i or i-Ng, j or j-Ng, l), the signed frequency below Ng/2.
+ *  - Shell edges are in units of k_f = 2 pi / L. Mode m is in shell n iff
+ *    e_n^2 <= |m|^2 < e_{n+1}^2 (integer |m|^2); k = 0 is in no shell.
+ *  - No exception crosses the ABI. Every call returns a bsp_status; on failure
+ *    bsp_last_error() gives a message (thread-local, valid until the next call on the
+ *    same thread). A CUDA error inside a call is reported as BSP_ERR_CUDA.
+ *  - The caller owns every buffer it passes. A plan owns its device tables, scratch and
+ *    cached shell fields. A plan is not safe for concurrent use from several threads.
+ *  - Calls taking a `stream` (a cudaStream_t, NULL = legacy default stream) enqueue their
+ *    GPU work on it and return without waiting, unless documented otherwise.
+ */
+#ifndef BISPEC_H
+#define BISPEC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define BSP_API __attribute__((visibility("default")))
+#else
+#define BSP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  BSP_OK = 0,
+  BSP_ERR_INVALID_ARG = 1,   /* a null pointer, a size or an enum out of range */
+  BSP_ERR_ALIASING = 2,      /* a shell reaches k >= 2 pi Ng / (3 L), the cap after Eq. (2.12) */
+  BSP_ERR_OOM = 3,           /* a device or host allocation failed */
+  BSP_ERR_CUDA = 4,          /* a CUDA runtime or launch error */
+  BSP_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up */
+  BSP_ERR_NOT_SUPPORTED = 6, /* a grid size or option this build does not handle */
+  BSP_ERR_NUMERIC = 7        /* a triangle count came out non-integral (Eq. (2.10)) */
+} bsp_status;
+
+typedef enum {
+  BSP_FP64 = 0,         /* FP64 shell FFTs and FP64 triple products */
+  BSP_FP32 = 1,         /* FP32 shell FFTs; FP32 products on CUDA cores, FP64 across chunks */
+  BSP_MIXED_BF16X3 = 2  /* FP32 shell FFTs; tcgen05 split-BF16 products (hi*hi + hi*lo + lo*hi),
+                           FP32 accumulation in tensor memory over short voxel runs, FP64 across */
+} bsp_precision;
+
+typedef struct {
+  int ng;                  /* grid points per side; even, 16..1024, of the form 2^p or 3*2^p */
+  double box_len;          /* L, the side of the periodic cube (any length unit) */
+  int n_shells;            /* N_s >= 1 */
+  const double* edges_kf;  /* host, N_s + 1 strictly increasing edges in units of k_f (Sec. 2.1) */
+  int n_mu, n_t;           /* (mu, t) cells over [0.5, 1]^2 (the region of Eq. (2.2)), >= 1 each */
+  int rsd;                 /* 1: multiply the spectrum by 1 + beta (k_z/|k|)^2 (Eq. (3.4)) */
+  double beta;             /* linear RSD parameter beta_1 of Eq. (3.4) */
+  int precision;           /* a bsp_precision */
+  size_t mem_budget_bytes; /* reserved, 0 */
+} bsp_plan_desc;
+
+/* One bin of triangles (Sec. 2.1): shells a >= b >= c and their labels (Eq. (2.4)). */
+typedef struct {
+  int a, b, c;         /* shell indices, a >= b >= c */
+  int i_mu, i_t;       /* (mu, t) cell after clamping mu and t to [0.5, 1] */
+  int inside;          /* 1 iff (mu, t) satisfies Eq. (2.2) */
+  double ntri;         /* N_tri of Eq. (2.9)/(2.10), an integer, ordered triples */
+  double tsum;         /* sum_x i_a i_b i_c = Ng^3 N_tri (FP64, as computed) */
+  double k1, k2, k3;   /* mean mode length of shells a, b, c, units of k_f (Sec. 2.1) */
+  double mu, t;        /* Eq. (2.4), unclamped */
+} bsp_triplet;
+
+typedef struct bsp_plan bsp_plan;
+
+/* Build the binning plan (Sec. 2.1) and the triangle counts N_tri of every bin (Eq. (2.10),
+ * computed on the GPU in FP64 from the counting fields of Eq. (2.11)); keep the bins with
+ * N_tri > 0. Synchronous: returns when the plan is ready. Allocates the plan's device memory
+ * on the current CUDA device with cudaMalloc. Errors: BSP_ERR_INVALID_ARG (desc null or out of
+ * range, edges not increasing, an empty shell), BSP_ERR_ALIASING (edge beyond the cap after
+ * Eq. (2.12)), BSP_ERR_NOT_SUPPORTED (ng), BSP_ERR_OOM, BSP_ERR_CUDA, BSP_ERR_NUMERIC. These
+ * argument checks run before any CUDA call, so they also work on a machine without a GPU.
+ * `stream`: the stream the plan's kernels use during creation. *out is NULL on failure. */
+BSP_API bsp_status bsp_plan_create(const bsp_plan_desc* desc, void* stream, bsp_plan** out);
+
+/* Free a plan and all its device memory (synchronises the device first). NULL is a no-op. */
+BSP_API bsp_status bsp_plan_destroy(bsp_plan* plan);
+
+/* Sizes of a plan: kept bins, shells, bytes of one shell-field set, device bytes held. */
+BSP_API bsp_status bsp_plan_info(const bsp_plan* plan, int* n_triplets, int* n_shells,
+                         size_t* field_bytes, size_t* device_bytes);
+
+/* The kept bins, in ascending (a, b, c) order; the host table is owned by the plan. */
+BSP_API bsp_status bsp_plan_triplets(const bsp_plan* plan, const bsp_triplet** table, int* n);
+
+/* Shell fields, Eq. (2.8): fields_out[n][x][y][z] = d_n(x) for n < N_s (device, caller-owned,
+ * N_s * Ng^3 reals: double for BSP_FP64 plans, float otherwise). With rsd=1 the Kaiser factor
+ * of Eq. (3.4) is applied to the spectrum first. spec: device half spectrum (see top). */
+BSP_API bsp_status bsp_shell_fields(bsp_plan* plan, const void* spec, void* fields_out, void* stream);
+
+/* Triple-product sums, the numerator of Eq. (2.7): msum[t] = sum_x d_a d_b d_c for every kept
+ * bin t, from shell fields laid out as bsp_shell_fields writes them (device, read-only).
+ * msum: device, n_triplets doubles. Uses the plan's contraction (bsp_precision). */
+BSP_API bsp_status bsp_contract(bsp_plan* plan, const void* fields, double* msum, void* stream);
+
+/* The whole estimator on one field, Eqs. (2.7)-(2.11) and the (mu, t) map:
+ *   b_triplet[t] = V_c^3 msum[t] / (V tsum[t])                        (device, n_triplets)
+ *   b_grid[a][i_mu][i_t] = V_c^3 sum msum / (V sum tsum) over the kept bins of k1 shell a in
+ *   that cell (merged bins, Sec. 2.1 last paragraph); NaN where no bin falls (device,
+ *   N_s * n_mu * n_t; may be NULL). spec: device half spectrum, read-only. */
+BSP_API bsp_status bsp_estimate(bsp_plan* plan, const void* spec, double* b_triplet, double* b_grid,
+                        void* stream);
+
+/* bsp_estimate from HOST buffers: copies the half spectrum host->device on `stream`, runs the
+ * estimator and copies b_triplet (and b_grid if not NULL) back to the host. Pinned host memory
+ * gives asynchronous copies; the call synchronises `stream` before it returns. */
+BSP_API bsp_status bsp_estimate_host(bsp_plan* plan, const void* spec_host, double* b_triplet_host,
+                             double* b_grid_host, void* stream);
+
+/* Per-bin numerators of the last bsp_estimate on this plan, msum[t] = sum_x d_a d_b d_c, as a
+ * device pointer owned by the plan (n_triplets doubles, valid until the next call on it). */
+BSP_API bsp_status bsp_last_sums(const bsp_plan* plan, const double** msum);
+
+/* Message of the last failing call on this thread ("" if none). */
+BSP_API const char* bsp_last_error(void);
+
+/* Library version string. */
+BSP_API const char* bsp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BISPEC_H */

@@ -1,0 +1,180 @@
+"""Thin Python binding of the C ABI (include/bispec.h) for torch device memory and streams.
+
+Every function with a `bsp_` name marshals its arguments and calls the C entry point of the
+same name; all arithmetic of the estimator runs in the library's CUDA kernels. `Plan` bundles
+a plan handle with torch tensors for its outputs.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import PRECISIONS, BispecError, PlanDesc, Triplet, check
+
+TRIPLET_DTYPE = np.dtype([("a", "i4"), ("b", "i4"), ("c", "i4"), ("i_mu", "i4"), ("i_t", "i4"),
+                          ("inside", "i4"), ("ntri", "f8"), ("tsum", "f8"), ("k1", "f8"),
+                          ("k2", "f8"), ("k3", "f8"), ("mu", "f8"), ("t", "f8")])
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _ptr(t) -> int:
+    return int(t.data_ptr())
+
+
+# ------------------------------------------------------------------ C names
+def bsp_plan_create(desc: PlanDesc, stream=None) -> C.c_void_p:
+    out = C.c_void_p()
+    check(_lib.load().bsp_plan_create(C.byref(desc), C.c_void_p(_stream_ptr(stream)), C.byref(out)))
+    return out
+
+
+def bsp_plan_destroy(handle) -> None:
+    check(_lib.load().bsp_plan_destroy(handle))
+
+
+def bsp_plan_info(handle):
+    nt, ns, fb, db = C.c_int(), C.c_int(), C.c_size_t(), C.c_size_t()
+    check(_lib.load().bsp_plan_info(handle, C.byref(nt), C.byref(ns), C.byref(fb), C.byref(db)))
+    return nt.value, ns.value, fb.value, db.value
+
+
+def bsp_plan_triplets(handle) -> np.ndarray:
+    tab = C.POINTER(Triplet)()
+    n = C.c_int()
+    check(_lib.load().bsp_plan_triplets(handle, C.byref(tab), C.byref(n)))
+    if n.value == 0:
+        return np.zeros(0, dtype=TRIPLET_DTYPE)
+    raw = C.string_at(C.cast(tab, C.c_void_p), n.value * C.sizeof(Triplet))
+    return np.frombuffer(raw, dtype=TRIPLET_DTYPE).copy()
+
+
+def bsp_shell_fields(handle, spec: torch.Tensor, fields_out: torch.Tensor, stream=None) -> None:
+    check(_lib.load().bsp_shell_fields(handle, C.c_void_p(_ptr(spec)), C.c_void_p(_ptr(fields_out)),
+                                       C.c_void_p(_stream_ptr(stream))))
+
+
+def bsp_contract(handle, fields: torch.Tensor, msum: torch.Tensor, stream=None) -> None:
+    check(_lib.load().bsp_contract(handle, C.c_void_p(_ptr(fields)), C.c_void_p(_ptr(msum)),
+                                   C.c_void_p(_stream_ptr(stream))))
+
+
+def bsp_estimate(handle, spec: torch.Tensor, b_triplet: torch.Tensor, b_grid, stream=None) -> None:
+    grid = C.c_void_p(_ptr(b_grid)) if b_grid is not None else C.c_void_p(0)
+    check(_lib.load().bsp_estimate(handle, C.c_void_p(_ptr(spec)), C.c_void_p(_ptr(b_triplet)), grid,
+                                   C.c_void_p(_stream_ptr(stream))))
+
+
+def bsp_estimate_host(handle, spec_host, b_triplet_host, b_grid_host, stream=None) -> None:
+    def hp(x):
+        if x is None:
+            return C.c_void_p(0)
+        return C.c_void_p(x.data_ptr() if isinstance(x, torch.Tensor) else x.ctypes.data)
+    check(_lib.load().bsp_estimate_host(handle, hp(spec_host), hp(b_triplet_host), hp(b_grid_host),
+                                        C.c_void_p(_stream_ptr(stream))))
+
+
+def bsp_last_sums(handle) -> int:
+    p = C.c_void_p()
+    check(_lib.load().bsp_last_sums(handle, C.byref(p)))
+    return p.value
+
+
+def bsp_version() -> str:
+    return _lib.load().bsp_version().decode()
+
+
+# ------------------------------------------------------------------ convenience object
+class Plan:
+    """A binning plan plus its output tensors on the current CUDA device.
+
+    ng, box_len, edges_kf: grid, box side and shell edges in units of k_f = 2 pi / L;
+    n_mu, n_t: (mu, t) cells; rsd/beta: linear RSD along z (Eq. (3.4));
+    precision: 'fp64', 'fp32' or 'mixed_bf16x3'."""
+
+    def __init__(self, ng, box_len, edges_kf, n_mu=10, n_t=10, rsd=False, beta=0.0,
+                 precision="fp32", stream=None):
+        self._edges = np.ascontiguousarray(np.asarray(edges_kf, dtype=np.float64))
+        desc = PlanDesc()
+        desc.ng = int(ng)
+        desc.box_len = float(box_len)
+        desc.n_shells = len(self._edges) - 1
+        desc.edges_kf = self._edges.ctypes.data_as(C.POINTER(C.c_double))
+        desc.n_mu = int(n_mu)
+        desc.n_t = int(n_t)
+        desc.rsd = 1 if rsd else 0
+        desc.beta = float(beta)
+        desc.precision = PRECISIONS[precision]
+        desc.mem_budget_bytes = 0
+        self.handle = None
+        self.handle = bsp_plan_create(desc, stream)
+        self.ng, self.box_len, self.n_mu, self.n_t = int(ng), float(box_len), int(n_mu), int(n_t)
+        self.precision = precision
+        self.real_dtype = torch.float64 if precision == "fp64" else torch.float32
+        self.complex_dtype = torch.complex128 if precision == "fp64" else torch.complex64
+        self.n_triplets, self.n_shells, self.field_bytes, self.device_bytes = bsp_plan_info(self.handle)
+        self.triplets = bsp_plan_triplets(self.handle)
+
+    def close(self):
+        if self.handle is not None:
+            bsp_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def spec_shape(self):
+        return (self.ng, self.ng, self.ng // 2 + 1)
+
+    def _check_spec(self, spec: torch.Tensor):
+        if not spec.is_cuda or spec.dtype != self.complex_dtype or tuple(spec.shape) != self.spec_shape() \
+                or not spec.is_contiguous():
+            raise ValueError(f"spec must be a contiguous CUDA {self.complex_dtype} tensor of shape "
+                             f"{self.spec_shape()}")
+
+    def estimate(self, spec: torch.Tensor, stream=None, with_grid=True):
+        """(b_triplet [n_triplets], b_grid [Ns, n_mu, n_t]) as float64 CUDA tensors."""
+        self._check_spec(spec)
+        dev = spec.device
+        b = torch.empty(self.n_triplets, dtype=torch.float64, device=dev)
+        g = torch.empty((self.n_shells, self.n_mu, self.n_t), dtype=torch.float64, device=dev) \
+            if with_grid else None
+        bsp_estimate(self.handle, spec, b, g, stream)
+        return b, g
+
+    def estimate_host(self, spec_host, stream=None):
+        """Host-in, host-out estimate (copies inside the call). spec_host: pinned torch or numpy."""
+        b = np.empty(self.n_triplets, dtype=np.float64)
+        g = np.empty((self.n_shells, self.n_mu, self.n_t), dtype=np.float64)
+        bsp_estimate_host(self.handle, spec_host, b, g, stream)
+        return b, g
+
+    def shell_fields(self, spec: torch.Tensor, stream=None) -> torch.Tensor:
+        self._check_spec(spec)
+        out = torch.empty((self.n_shells, self.ng, self.ng, self.ng), dtype=self.real_dtype,
+                          device=spec.device)
+        bsp_shell_fields(self.handle, spec, out, stream)
+        return out
+
+    def contract(self, fields: torch.Tensor, stream=None) -> torch.Tensor:
+        if not fields.is_cuda or fields.dtype != self.real_dtype or not fields.is_contiguous() \
+                or fields.numel() != self.n_shells * self.ng ** 3:
+            raise ValueError("fields must be the contiguous [Ns, Ng, Ng, Ng] output of shell_fields")
+        msum = torch.empty(self.n_triplets, dtype=torch.float64, device=fields.device)
+        bsp_contract(self.handle, fields, msum, stream)
+        return msum
+
+
+__all__ = ["Plan", "BispecError", "bsp_plan_create", "bsp_plan_destroy", "bsp_plan_info",
+           "bsp_plan_triplets", "bsp_shell_fields", "bsp_contract", "bsp_estimate",
+           "bsp_estimate_host", "bsp_last_sums", "bsp_version", "TRIPLET_DTYPE"]

@@ -1,0 +1,650 @@
+// C ABI of the bispectrum library: plan construction (Sec. 2.1 binning, Eq. (2.10) counts),
+// the estimator (Eqs. (2.7)-(2.11)) and the (mu, t) map (Eq. (2.4)).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace bsp {
+
+static thread_local std::string g_error;
+
+void set_error(const std::string& msg) { g_error = msg; }
+
+bsp_status fail(bsp_status s, const std::string& msg) {
+  g_error = msg;
+  return s;
+}
+
+bsp_status cuda_fail(cudaError_t e, const char* what) {
+  g_error = std::string("CUDA error in ") + what + ": " + cudaGetErrorString(e);
+  if (e == cudaErrorMemoryAllocation) return BSP_ERR_OOM;
+  return BSP_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------- host-side helpers
+static long long isqrt_ll(long long v) {
+  if (v < 0) return -1;
+  long long r = (long long)sqrt((double)v);
+  while (r * r > v) --r;
+  while ((r + 1) * (r + 1) <= v) ++r;
+  return r;
+}
+
+// FFT stage list: radix 8 while possible, then 4, 2 and 3.
+static bool make_stages(int n, FftStages* st) {
+  st->n = n;
+  st->nst = 0;
+  int m = n;
+  while (m % 8 == 0 && st->nst < kMaxStages) { st->radix[st->nst++] = 8; m /= 8; }
+  while (m % 4 == 0 && st->nst < kMaxStages) { st->radix[st->nst++] = 4; m /= 4; }
+  while (m % 2 == 0 && st->nst < kMaxStages) { st->radix[st->nst++] = 2; m /= 2; }
+  while (m % 3 == 0 && st->nst < kMaxStages) { st->radix[st->nst++] = 3; m /= 3; }
+  return m == 1;
+}
+
+// Device allocation owned by a plan.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace bsp
+
+using namespace bsp;
+
+struct bsp_plan {
+  // description
+  int ng = 0, ns = 0, n_mu = 0, n_t = 0, rsd = 0, prec = 0;
+  double box_len = 0.0, beta = 0.0;
+  std::vector<double> edges;
+  std::vector<long long> q;       // integer thresholds Q_n
+  std::vector<long long> nmodes;  // modes per shell
+  std::vector<double> kbar;       // mean |m| per shell
+  std::vector<ShellGeom> geom;
+  std::vector<bsp_triplet> trips;  // kept bins
+  FftStages st_full{}, st_half{};
+  int lines_xy = 0, lines_z = 0;
+  int n_sm = 0;
+  // device buffers
+  std::vector<DevBuf> bufs;
+  size_t dev_bytes = 0;
+  void* tw = nullptr;
+  ShellGeom* d_geom = nullptr;
+  Item *d_xi = nullptr, *d_yi = nullptr, *d_zi = nullptr;
+  int nxi = 0, nyi = 0, nzi = 0;
+  void *g1 = nullptr, *g2 = nullptr, *fields = nullptr;
+  // contraction tables (kept bins)
+  Tile* d_tiles = nullptr;
+  int2* d_pairs = nullptr;
+  int* d_map = nullptr;
+  int ntiles = 0;
+  int gridx = 0;
+  double* partial = nullptr;
+  double* msum = nullptr;
+  double* tsum = nullptr;
+  int* cell_ptr = nullptr;
+  int* cell_idx = nullptr;
+  // host staging for bsp_estimate_host
+  void* spec_dev = nullptr;
+  double* btrip_dev = nullptr;
+  double* bgrid_dev = nullptr;
+
+  size_t elem() const { return prec == BSP_FP64 ? sizeof(double) : sizeof(float); }
+  long long nvox() const { return (long long)ng * ng * ng; }
+  int n_cells() const { return ns * n_mu * n_t; }
+  size_t spec_bytes() const { return (size_t)ng * ng * (ng / 2 + 1) * 2 * elem(); }
+  size_t field_bytes() const { return (size_t)ns * (size_t)nvox() * elem(); }
+};
+
+namespace {
+
+bsp_status dev_alloc(bsp_plan* p, size_t bytes, void** out) {
+  *out = nullptr;
+  if (bytes == 0) bytes = 16;
+  void* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(BSP_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " +
+                                 cudaGetErrorString(e));
+  }
+  p->bufs.push_back({d, bytes});
+  p->dev_bytes += bytes;
+  *out = d;
+  return BSP_OK;
+}
+
+template <typename V>
+bsp_status dev_upload(bsp_plan* p, const std::vector<V>& h, V** out, cudaStream_t s) {
+  void* d = nullptr;
+  bsp_status st = dev_alloc(p, h.size() * sizeof(V), &d);
+  if (st != BSP_OK) return st;
+  if (!h.empty()) BSP_CUDA(cudaMemcpyAsync(d, h.data(), h.size() * sizeof(V), cudaMemcpyHostToDevice, s));
+  *out = static_cast<V*>(d);
+  return BSP_OK;
+}
+
+void dev_free(bsp_plan* p, void* d) {
+  for (size_t i = 0; i < p->bufs.size(); ++i) {
+    if (p->bufs[i].p == d) {
+      cudaFree(d);
+      p->dev_bytes -= p->bufs[i].bytes;
+      p->bufs.erase(p->bufs.begin() + i);
+      return;
+    }
+  }
+}
+
+int fft_lines_for(int len, int prec) {
+  const int e = prec == BSP_FP64 ? FftElems<double>::value : FftElems<float>::value;
+  int l = e * kFftThreads / len;
+  return l < 1 ? 1 : l;
+}
+
+void make_items(const bsp_plan* p, int lines_xy, int lines_z, std::vector<Item>& xi,
+                std::vector<Item>& yi, std::vector<Item>& zi) {
+  const int ng = p->ng;
+  xi.clear(); yi.clear(); zi.clear();
+  for (int n = 0; n < p->ns; ++n) {
+    const ShellGeom& g = p->geom[n];
+    const int r = g.r;
+    for (int ky = -(r - 1); ky <= r - 1; ++ky) {
+      const long long rem = (long long)g.qhi - 1 - (long long)ky * ky;
+      const int kzmax = (int)isqrt_ll(rem) + 1;  // kz with ky^2 + kz^2 < qhi
+      for (int kz0 = 0; kz0 < kzmax; kz0 += lines_xy)
+        xi.push_back({n, ky, kz0, std::min(lines_xy, kzmax - kz0)});
+    }
+    for (int x = 0; x < ng; ++x)
+      for (int kz0 = 0; kz0 < r; kz0 += lines_xy) yi.push_back({n, x, kz0, std::min(lines_xy, r - kz0)});
+    for (int x = 0; x < ng; ++x)
+      for (int y0 = 0; y0 < ng; y0 += lines_z) zi.push_back({n, x, y0, std::min(lines_z, ng - y0)});
+  }
+}
+
+// Tiles of up to 4 consecutive pairs x 4 consecutive c over a list of bins sorted by (a, b, c).
+void make_tiles(const std::vector<int>& ta, const std::vector<int>& tb, const std::vector<int>& tc,
+                std::vector<int2>& pairs, std::vector<Tile>& tiles, std::vector<int>& map) {
+  pairs.clear(); tiles.clear(); map.clear();
+  std::vector<std::vector<std::pair<int, int>>> pc;  // per pair: (c, bin)
+  for (size_t t = 0; t < ta.size(); ++t) {
+    if (pairs.empty() || pairs.back().x != ta[t] || pairs.back().y != tb[t]) {
+      pairs.push_back(make_int2(ta[t], tb[t]));
+      pc.emplace_back();
+    }
+    pc.back().push_back({tc[t], (int)t});
+  }
+  const int np = (int)pairs.size();
+  for (int p0 = 0; p0 < np; p0 += 4) {
+    const int cnt = std::min(4, np - p0);
+    int cmin = 1 << 30, cmax = -1;
+    for (int i = 0; i < cnt; ++i)
+      for (auto& e : pc[p0 + i]) { cmin = std::min(cmin, e.first); cmax = std::max(cmax, e.first); }
+    for (int c0 = cmin - cmin % 4; c0 <= cmax; c0 += 4) {
+      int m[16];
+      bool any = false;
+      for (int k = 0; k < 16; ++k) m[k] = -1;
+      for (int i = 0; i < cnt; ++i)
+        for (auto& e : pc[p0 + i])
+          if (e.first >= c0 && e.first < c0 + 4) { m[i * 4 + (e.first - c0)] = e.second; any = true; }
+      if (!any) continue;
+      tiles.push_back({p0, cnt, c0, 0});
+      for (int k = 0; k < 16; ++k) map.push_back(m[k]);
+    }
+  }
+}
+
+// Shell fields of one precision: X, Y, Z passes for every shell.
+template <typename T>
+bsp_status run_passes(const bsp_plan* p, const void* spec, int rsd, void* tw, void* g1, void* g2,
+                      void* fields, const Item* xi, int nxi, const Item* yi, int nyi, const Item* zi,
+                      int nzi, int lines_xy, int lines_z, cudaStream_t s) {
+  PassArgs a{};
+  a.spec = spec;
+  a.g1 = g1;
+  a.g2 = g2;
+  a.fields = fields;
+  a.tw = tw;
+  a.geom = p->d_geom;
+  a.ng = p->ng;
+  a.rsd = rsd;
+  a.beta = p->beta;
+  a.st = p->st_full;
+  a.items = xi;
+  bsp_status st = launch_xpass<T>(a, nxi, lines_xy, s);
+  if (st != BSP_OK) return st;
+  a.items = yi;
+  st = launch_ypass<T>(a, nyi, lines_xy, s);
+  if (st != BSP_OK) return st;
+  a.items = zi;
+  a.st = p->st_half;
+  return launch_zpass<T>(a, nzi, lines_z, s);
+}
+
+int pick_gridx(const bsp_plan* p, int ntiles) {
+  const int gy = (ntiles + 255) / 256;
+  int gx = (4 * p->n_sm) / std::max(gy, 1);
+  gx = std::max(gx, 1);
+  const long long chunks = (p->nvox() + 63) / 64;
+  if (gx > chunks) gx = (int)chunks;
+  return gx;
+}
+
+bsp_status validate(const bsp_plan_desc* d) {
+  if (!d) return fail(BSP_ERR_INVALID_ARG, "desc is NULL");
+  if (d->ng < 16 || d->ng > 1024 || (d->ng % 2) != 0)
+    return fail(BSP_ERR_NOT_SUPPORTED, "ng must be even and within [16, 1024]");
+  FftStages st;
+  if (!make_stages(d->ng, &st) || !make_stages(d->ng / 2, &st))
+    return fail(BSP_ERR_NOT_SUPPORTED, "ng must be a product of 2s and 3s");
+  if (!(d->box_len > 0.0) || !isfinite(d->box_len)) return fail(BSP_ERR_INVALID_ARG, "box_len must be > 0");
+  if (d->n_shells < 1 || d->n_shells > 256) return fail(BSP_ERR_INVALID_ARG, "n_shells out of range");
+  if (!d->edges_kf) return fail(BSP_ERR_INVALID_ARG, "edges_kf is NULL");
+  for (int i = 0; i <= d->n_shells; ++i)
+    if (!isfinite(d->edges_kf[i]) || d->edges_kf[i] < 0.0) return fail(BSP_ERR_INVALID_ARG, "bad edge");
+  for (int i = 0; i < d->n_shells; ++i)
+    if (!(d->edges_kf[i + 1] > d->edges_kf[i])) return fail(BSP_ERR_INVALID_ARG, "edges must increase");
+  if (d->n_mu < 1 || d->n_t < 1 || d->n_mu > 4096 || d->n_t > 4096)
+    return fail(BSP_ERR_INVALID_ARG, "n_mu and n_t must be >= 1");
+  if (d->precision < BSP_FP64 || d->precision > BSP_MIXED_BF16X3)
+    return fail(BSP_ERR_INVALID_ARG, "unknown precision");
+  if (d->rsd != 0 && d->rsd != 1) return fail(BSP_ERR_INVALID_ARG, "rsd must be 0 or 1");
+  if (d->rsd && !isfinite(d->beta)) return fail(BSP_ERR_INVALID_ARG, "beta must be finite");
+  return BSP_OK;
+}
+
+// Host part of the plan (Sec. 2.1): thresholds, cap, mode counts, means, geometry.
+bsp_status host_plan(bsp_plan* p, const bsp_plan_desc* d) {
+  p->ng = d->ng;
+  p->ns = d->n_shells;
+  p->n_mu = d->n_mu;
+  p->n_t = d->n_t;
+  p->rsd = d->rsd;
+  p->beta = d->rsd ? d->beta : 0.0;
+  p->prec = d->precision;
+  p->box_len = d->box_len;
+  p->edges.assign(d->edges_kf, d->edges_kf + d->n_shells + 1);
+  p->q.resize(p->ns + 1);
+  for (int n = 0; n <= p->ns; ++n) {
+    const double e = p->edges[n];
+    p->q[n] = (long long)ceil(e * e);
+  }
+  p->q[0] = std::max(1LL, p->q[0]);
+  for (int n = 0; n < p->ns; ++n)
+    if (p->q[n + 1] <= p->q[n]) return fail(BSP_ERR_INVALID_ARG, "shell " + std::to_string(n) + " is empty");
+  const long long qmax = p->q[p->ns];
+  // cap after Eq. (2.12): every mode |m| < Ng/3  <=>  9 (Q_Ns - 1) < Ng^2
+  if (9 * (qmax - 1) >= (long long)p->ng * p->ng)
+    return fail(BSP_ERR_ALIASING, "largest shell reaches k >= 2 pi Ng / (3 L)");
+  // mode counts per |m|^2
+  const long long rr = isqrt_ll(qmax - 1);
+  std::vector<long long> cnt(qmax, 0);
+  for (long long x = -rr; x <= rr; ++x)
+    for (long long y = -rr; y <= rr; ++y) {
+      const long long qxy = x * x + y * y;
+      if (qxy >= qmax) continue;
+      for (long long z = -rr; z <= rr; ++z) {
+        const long long qq = qxy + z * z;
+        if (qq < qmax) cnt[qq] += 1;
+      }
+    }
+  p->nmodes.assign(p->ns, 0);
+  p->kbar.assign(p->ns, 0.0);
+  for (int n = 0; n < p->ns; ++n) {
+    double s = 0.0;
+    long long c = 0;
+    for (long long qq = p->q[n]; qq < p->q[n + 1]; ++qq) {
+      if (cnt[qq]) {
+        s += (double)cnt[qq] * sqrt((double)qq);
+        c += cnt[qq];
+      }
+    }
+    if (c == 0) return fail(BSP_ERR_INVALID_ARG, "shell " + std::to_string(n) + " holds no modes");
+    p->nmodes[n] = c;
+    p->kbar[n] = s / (double)c;
+  }
+  make_stages(p->ng, &p->st_full);
+  make_stages(p->ng / 2, &p->st_half);
+  // geometry: complex offsets of each shell in the X and Y pass buffers
+  p->geom.resize(p->ns);
+  long long o1 = 0, o2 = 0;
+  for (int n = 0; n < p->ns; ++n) {
+    ShellGeom& g = p->geom[n];
+    g.qlo = (int)p->q[n];
+    g.qhi = (int)p->q[n + 1];
+    g.r = (int)isqrt_ll(p->q[n + 1] - 1) + 1;
+    g.pad = 0;
+    g.g1_off = o1;
+    g.g2_off = o2;
+    o1 += (long long)p->ng * (2 * g.r - 1) * g.r;
+    o2 += (long long)p->ng * p->ng * g.r;
+  }
+  return BSP_OK;
+}
+
+long long g1_elems(const bsp_plan* p) {
+  const ShellGeom& g = p->geom.back();
+  return g.g1_off + (long long)p->ng * (2 * g.r - 1) * g.r;
+}
+long long g2_elems(const bsp_plan* p) {
+  const ShellGeom& g = p->geom.back();
+  return g.g2_off + (long long)p->ng * p->ng * g.r;
+}
+
+// Eq. (2.10) in FP64 on the GPU for the candidate bins: T_abc = sum_x i_a i_b i_c.
+bsp_status count_triangles(bsp_plan* p, const std::vector<int>& ca, const std::vector<int>& cb,
+                           const std::vector<int>& cc, std::vector<double>& tsum, cudaStream_t s) {
+  const int lxy = fft_lines_for(p->ng, BSP_FP64);
+  const int lz = fft_lines_for(p->ng / 2, BSP_FP64);
+  std::vector<Item> xi, yi, zi;
+  make_items(p, lxy, lz, xi, yi, zi);
+  std::vector<void*> tmp;
+  auto cleanup = [&]() {
+    cudaStreamSynchronize(s);
+    for (void* d : tmp) dev_free(p, d);
+  };
+  void *tw = nullptr, *g1 = nullptr, *g2 = nullptr, *f = nullptr;
+  Item *dxi = nullptr, *dyi = nullptr, *dzi = nullptr;
+  bsp_status st;
+#define TRY(x) do { st = (x); if (st != BSP_OK) { cleanup(); return st; } } while (0)
+  TRY(dev_alloc(p, p->ng * sizeof(double2), &tw)); tmp.push_back(tw);
+  TRY(dev_alloc(p, g1_elems(p) * sizeof(double2), &g1)); tmp.push_back(g1);
+  TRY(dev_alloc(p, g2_elems(p) * sizeof(double2), &g2)); tmp.push_back(g2);
+  TRY(dev_alloc(p, (size_t)p->ns * p->nvox() * sizeof(double), &f)); tmp.push_back(f);
+  TRY(dev_upload(p, xi, &dxi, s)); tmp.push_back(dxi);
+  TRY(dev_upload(p, yi, &dyi, s)); tmp.push_back(dyi);
+  TRY(dev_upload(p, zi, &dzi, s)); tmp.push_back(dzi);
+  TRY(launch_twiddles<double>(tw, p->ng, s));
+  TRY(run_passes<double>(p, nullptr, 0, tw, g1, g2, f, dxi, (int)xi.size(), dyi, (int)yi.size(), dzi,
+                         (int)zi.size(), lxy, lz, s));
+  std::vector<int2> pairs;
+  std::vector<Tile> tiles;
+  std::vector<int> map;
+  make_tiles(ca, cb, cc, pairs, tiles, map);
+  Tile* dt = nullptr; int2* dp = nullptr; int* dm = nullptr;
+  TRY(dev_upload(p, tiles, &dt, s)); tmp.push_back(dt);
+  TRY(dev_upload(p, pairs, &dp, s)); tmp.push_back(dp);
+  TRY(dev_upload(p, map, &dm, s)); tmp.push_back(dm);
+  ContractArgs c{};
+  c.fields = f;
+  c.nvox = p->nvox();
+  c.ns = p->ns;
+  c.tiles = dt;
+  c.pairs = dp;
+  c.tile_map = dm;
+  c.ntiles = (int)tiles.size();
+  c.gridx = pick_gridx(p, c.ntiles);
+  void* part = nullptr; void* ms = nullptr;
+  TRY(dev_alloc(p, (size_t)c.gridx * c.ntiles * 16 * sizeof(double), &part)); tmp.push_back(part);
+  TRY(dev_alloc(p, ca.size() * sizeof(double), &ms)); tmp.push_back(ms);
+  c.partial = static_cast<double*>(part);
+  c.msum = static_cast<double*>(ms);
+  c.n_out = (int)ca.size();
+  TRY(launch_contract_simt<double>(c, s));
+  TRY(launch_reduce_partials(c, s));
+  tsum.assign(ca.size(), 0.0);
+  cudaError_t e = cudaMemcpyAsync(tsum.data(), ms, ca.size() * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "triangle counts"); }
+  cleanup();
+#undef TRY
+  return BSP_OK;
+}
+
+template <typename T>
+bsp_status estimate_impl(bsp_plan* p, const void* spec, double* b_trip, double* b_grid, cudaStream_t s) {
+  bsp_status st = run_passes<T>(p, spec, p->rsd, p->tw, p->g1, p->g2, p->fields, p->d_xi, p->nxi,
+                                p->d_yi, p->nyi, p->d_zi, p->nzi, p->lines_xy, p->lines_z, s);
+  if (st != BSP_OK) return st;
+  ContractArgs c{};
+  c.fields = p->fields;
+  c.nvox = p->nvox();
+  c.ns = p->ns;
+  c.tiles = p->d_tiles;
+  c.pairs = p->d_pairs;
+  c.tile_map = p->d_map;
+  c.ntiles = p->ntiles;
+  c.gridx = p->gridx;
+  c.partial = p->partial;
+  c.msum = p->msum;
+  c.n_out = (int)p->trips.size();
+  st = launch_contract_simt<T>(c, s);
+  if (st != BSP_OK) return st;
+  st = launch_reduce_partials(c, s);
+  if (st != BSP_OK) return st;
+  FinalizeArgs f{};
+  f.msum = p->msum;
+  f.tsum = p->tsum;
+  f.n_trip = (int)p->trips.size();
+  f.cell_ptr = p->cell_ptr;
+  f.cell_idx = p->cell_idx;
+  f.n_cells = p->n_cells();
+  const double vc = pow(p->box_len / p->ng, 3.0);
+  f.norm = vc * vc * vc / (p->box_len * p->box_len * p->box_len);
+  f.b_trip = b_trip;
+  f.b_grid = b_grid;
+  return launch_finalize(f, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* bsp_last_error(void) { return g_error.c_str(); }
+
+const char* bsp_version(void) { return "bispec-gb300 0.1 (sm_103a)"; }
+
+bsp_status bsp_plan_create(const bsp_plan_desc* desc, void* stream, bsp_plan** out) {
+  if (!out) return fail(BSP_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  g_error.clear();
+  bsp_status st = validate(desc);
+  if (st != BSP_OK) return st;
+  bsp_plan* p = new (std::nothrow) bsp_plan();
+  if (!p) return fail(BSP_ERR_OOM, "host allocation failed");
+  st = host_plan(p, desc);
+  if (st != BSP_OK) { delete p; return st; }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->n_sm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) { delete p; return cuda_fail(e, "device query"); }
+  // candidate bins: the triangle inequality on the extreme mode lengths
+  std::vector<int> ca, cb, cc;
+  for (int a = 0; a < p->ns; ++a)
+    for (int b = 0; b <= a; ++b)
+      for (int c = 0; c <= b; ++c) {
+        const double qa = (double)p->q[a];
+        const double qb = (double)(p->q[b + 1] - 1);
+        const double qc = (double)(p->q[c + 1] - 1);
+        if (sqrt(qa) <= sqrt(qb) + sqrt(qc)) { ca.push_back(a); cb.push_back(b); cc.push_back(c); }
+      }
+  // geometry on the device (shared by the FP64 count and the estimator)
+  st = dev_upload(p, p->geom, &p->d_geom, s);
+  if (st != BSP_OK) { bsp_plan_destroy(p); return st; }
+  std::vector<double> tsum;
+  st = count_triangles(p, ca, cb, cc, tsum, s);
+  if (st != BSP_OK) { bsp_plan_destroy(p); return st; }
+  const double ng3 = (double)p->nvox();
+  std::vector<int> ka, kb, kc;
+  std::vector<double> kt;
+  for (size_t i = 0; i < ca.size(); ++i) {
+    const double nt = tsum[i] / ng3;
+    const double rn = rint(nt);
+    if (fabs(nt - rn) > 1e-3) {
+      bsp_plan_destroy(p);
+      return fail(BSP_ERR_NUMERIC, "non-integral triangle count for bin (" + std::to_string(ca[i]) + "," +
+                                       std::to_string(cb[i]) + "," + std::to_string(cc[i]) + ")");
+    }
+    if (rn <= 0.0) continue;
+    ka.push_back(ca[i]); kb.push_back(cb[i]); kc.push_back(cc[i]);
+    kt.push_back(tsum[i]);
+    bsp_triplet t{};
+    t.a = ca[i]; t.b = cb[i]; t.c = cc[i];
+    t.ntri = rn;
+    t.tsum = tsum[i];
+    const double k1 = p->kbar[t.a], k2 = p->kbar[t.b], k3 = p->kbar[t.c];
+    t.k1 = k1; t.k2 = k2; t.k3 = k3;
+    t.t = k2 / k1;
+    t.mu = 0.5 * (k1 / k2 + k2 / k1 - (k3 / k1) * (k3 / k2));
+    const double mc = std::min(std::max(t.mu, 0.5), 1.0);
+    const double tc = std::min(std::max(t.t, 0.5), 1.0);
+    t.i_mu = std::min((int)floor((mc - 0.5) * (2.0 * p->n_mu)), p->n_mu - 1);
+    t.i_t = std::min((int)floor((tc - 0.5) * (2.0 * p->n_t)), p->n_t - 1);
+    t.inside = (t.t >= 0.5 && t.t <= 1.0 && t.mu >= 0.5 && t.mu <= 1.0 && 2.0 * t.mu * t.t >= 1.0) ? 1 : 0;
+    p->trips.push_back(t);
+  }
+  // estimator buffers in the plan's precision
+  p->lines_xy = fft_lines_for(p->ng, p->prec);
+  p->lines_z = fft_lines_for(p->ng / 2, p->prec);
+  std::vector<Item> xi, yi, zi;
+  make_items(p, p->lines_xy, p->lines_z, xi, yi, zi);
+  p->nxi = (int)xi.size(); p->nyi = (int)yi.size(); p->nzi = (int)zi.size();
+  const size_t ce = p->prec == BSP_FP64 ? sizeof(double2) : sizeof(float2);
+  std::vector<int2> pairs;
+  std::vector<Tile> tiles;
+  std::vector<int> map;
+  make_tiles(ka, kb, kc, pairs, tiles, map);
+  p->ntiles = (int)tiles.size();
+  p->gridx = pick_gridx(p, p->ntiles);
+  std::vector<int> cptr(p->n_cells() + 1, 0), cidx;
+  {
+    std::vector<std::vector<int>> cells(p->n_cells());
+    for (size_t t = 0; t < p->trips.size(); ++t) {
+      const bsp_triplet& b = p->trips[t];
+      cells[(b.a * p->n_mu + b.i_mu) * p->n_t + b.i_t].push_back((int)t);
+    }
+    for (int c = 0; c < p->n_cells(); ++c) {
+      cptr[c + 1] = cptr[c] + (int)cells[c].size();
+      cidx.insert(cidx.end(), cells[c].begin(), cells[c].end());
+    }
+  }
+#define TRY(x) do { st = (x); if (st != BSP_OK) { bsp_plan_destroy(p); return st; } } while (0)
+  TRY(dev_alloc(p, p->ng * ce, &p->tw));
+  TRY(p->prec == BSP_FP64 ? launch_twiddles<double>(p->tw, p->ng, s) : launch_twiddles<float>(p->tw, p->ng, s));
+  TRY(dev_upload(p, xi, &p->d_xi, s));
+  TRY(dev_upload(p, yi, &p->d_yi, s));
+  TRY(dev_upload(p, zi, &p->d_zi, s));
+  TRY(dev_alloc(p, g1_elems(p) * ce, &p->g1));
+  TRY(dev_alloc(p, g2_elems(p) * ce, &p->g2));
+  TRY(dev_alloc(p, p->field_bytes(), &p->fields));
+  TRY(dev_upload(p, tiles, &p->d_tiles, s));
+  TRY(dev_upload(p, pairs, &p->d_pairs, s));
+  TRY(dev_upload(p, map, &p->d_map, s));
+  void* tmp = nullptr;
+  TRY(dev_alloc(p, (size_t)std::max(p->gridx, 1) * std::max(p->ntiles, 1) * 16 * sizeof(double), &tmp));
+  p->partial = static_cast<double*>(tmp);
+  TRY(dev_alloc(p, std::max<size_t>(p->trips.size(), 1) * sizeof(double), &tmp));
+  p->msum = static_cast<double*>(tmp);
+  TRY(dev_upload(p, kt, &p->tsum, s));
+  TRY(dev_upload(p, cptr, &p->cell_ptr, s));
+  TRY(dev_upload(p, cidx, &p->cell_idx, s));
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) { bsp_plan_destroy(p); return cuda_fail(e, "plan upload"); }
+#undef TRY
+  *out = p;
+  return BSP_OK;
+}
+
+bsp_status bsp_plan_destroy(bsp_plan* p) {
+  if (!p) return BSP_OK;
+  cudaDeviceSynchronize();
+  for (auto& b : p->bufs) cudaFree(b.p);
+  p->bufs.clear();
+  delete p;
+  return BSP_OK;
+}
+
+bsp_status bsp_plan_info(const bsp_plan* p, int* n_triplets, int* n_shells, size_t* field_bytes,
+                         size_t* device_bytes) {
+  if (!p) return fail(BSP_ERR_INVALID_ARG, "plan is NULL");
+  if (n_triplets) *n_triplets = (int)p->trips.size();
+  if (n_shells) *n_shells = p->ns;
+  if (field_bytes) *field_bytes = p->field_bytes();
+  if (device_bytes) *device_bytes = p->dev_bytes;
+  return BSP_OK;
+}
+
+bsp_status bsp_plan_triplets(const bsp_plan* p, const bsp_triplet** table, int* n) {
+  if (!p || !table || !n) return fail(BSP_ERR_INVALID_ARG, "NULL argument");
+  *table = p->trips.data();
+  *n = (int)p->trips.size();
+  return BSP_OK;
+}
+
+bsp_status bsp_shell_fields(bsp_plan* p, const void* spec, void* fields_out, void* stream) {
+  if (!p || !spec || !fields_out) return fail(BSP_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (p->prec == BSP_FP64)
+    return run_passes<double>(p, spec, p->rsd, p->tw, p->g1, p->g2, fields_out, p->d_xi, p->nxi, p->d_yi,
+                              p->nyi, p->d_zi, p->nzi, p->lines_xy, p->lines_z, s);
+  return run_passes<float>(p, spec, p->rsd, p->tw, p->g1, p->g2, fields_out, p->d_xi, p->nxi, p->d_yi,
+                           p->nyi, p->d_zi, p->nzi, p->lines_xy, p->lines_z, s);
+}
+
+bsp_status bsp_contract(bsp_plan* p, const void* fields, double* msum, void* stream) {
+  if (!p || !fields || !msum) return fail(BSP_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ContractArgs c{};
+  c.fields = fields;
+  c.nvox = p->nvox();
+  c.ns = p->ns;
+  c.tiles = p->d_tiles;
+  c.pairs = p->d_pairs;
+  c.tile_map = p->d_map;
+  c.ntiles = p->ntiles;
+  c.gridx = p->gridx;
+  c.partial = p->partial;
+  c.msum = msum;
+  c.n_out = (int)p->trips.size();
+  bsp_status st = p->prec == BSP_FP64 ? launch_contract_simt<double>(c, s) : launch_contract_simt<float>(c, s);
+  if (st != BSP_OK) return st;
+  return launch_reduce_partials(c, s);
+}
+
+bsp_status bsp_estimate(bsp_plan* p, const void* spec, double* b_triplet, double* b_grid, void* stream) {
+  if (!p || !spec || !b_triplet) return fail(BSP_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (p->prec == BSP_FP64) return estimate_impl<double>(p, spec, b_triplet, b_grid, s);
+  return estimate_impl<float>(p, spec, b_triplet, b_grid, s);
+}
+
+bsp_status bsp_estimate_host(bsp_plan* p, const void* spec_host, double* b_triplet_host, double* b_grid_host,
+                             void* stream) {
+  if (!p || !spec_host || !b_triplet_host) return fail(BSP_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  bsp_status st;
+  if (!p->spec_dev) {
+    st = dev_alloc(p, p->spec_bytes(), &p->spec_dev);
+    if (st != BSP_OK) return st;
+    void* t = nullptr;
+    st = dev_alloc(p, std::max<size_t>(p->trips.size(), 1) * sizeof(double), &t);
+    if (st != BSP_OK) return st;
+    p->btrip_dev = static_cast<double*>(t);
+    st = dev_alloc(p, (size_t)p->n_cells() * sizeof(double), &t);
+    if (st != BSP_OK) return st;
+    p->bgrid_dev = static_cast<double*>(t);
+  }
+  BSP_CUDA(cudaMemcpyAsync(p->spec_dev, spec_host, p->spec_bytes(), cudaMemcpyHostToDevice, s));
+  st = bsp_estimate(p, p->spec_dev, p->btrip_dev, b_grid_host ? p->bgrid_dev : nullptr, stream);
+  if (st != BSP_OK) return st;
+  BSP_CUDA(cudaMemcpyAsync(b_triplet_host, p->btrip_dev, p->trips.size() * sizeof(double),
+                           cudaMemcpyDeviceToHost, s));
+  if (b_grid_host)
+    BSP_CUDA(cudaMemcpyAsync(b_grid_host, p->bgrid_dev, (size_t)p->n_cells() * sizeof(double),
+                             cudaMemcpyDeviceToHost, s));
+  BSP_CUDA(cudaStreamSynchronize(s));
+  return BSP_OK;
+}
+
+bsp_status bsp_last_sums(const bsp_plan* p, const double** msum) {
+  if (!p || !msum) return fail(BSP_ERR_INVALID_ARG, "NULL argument");
+  *msum = p->msum;
+  return BSP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,157 @@
+// Triple-product reduction on CUDA cores and the final normalisation.
+//
+// msum[t] = sum_x d_a(x) d_b(x) d_c(x) for every kept bin t = (a, b, c) (numerator of Eq. (2.7);
+// with counting fields, the T_abc of Eq. (2.10)). The bins are grouped as
+// M[(a,b), c] = sum_x (d_a d_b)(x) d_c(x): a tile owns up to 4 pairs (a, b) and 4 consecutive
+// c, i.e. 16 outputs held in registers by one thread. A block walks a contiguous voxel range in
+// chunks staged in shared memory (all shells of the chunk), so every field value read from
+// HBM serves every tile of the block. FP32 plans accumulate in FP32 over kFlushChunks chunks
+// and then add into FP64; FP64 plans accumulate in FP64. Blocks write FP64 partial sums,
+// which a second kernel adds in a fixed order (deterministic results).
+#include "common.cuh"
+
+namespace bsp {
+
+constexpr int kChunk = 64;         // voxels per shared-memory chunk
+constexpr int kContractThreads = 256;
+constexpr int kFlushChunks = 16;   // FP32 run length: 1024 voxels
+
+template <typename T>
+__global__ void __launch_bounds__(kContractThreads)
+contract_simt_kernel(ContractArgs a, long long vox_per_block) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* dsm = reinterpret_cast<T*>(smem_raw);   // [ns][kChunk + 1]
+  constexpr int LD = kChunk + 1;
+  const T* fields = static_cast<const T*>(a.fields);
+  const int tile = blockIdx.y * kContractThreads + threadIdx.x;
+  const bool active = tile < a.ntiles;
+  int ia[4], ib[4], c0 = 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) { ia[i] = 0; ib[i] = 0; }
+  if (active) {
+    const Tile t = a.tiles[tile];
+    c0 = t.c0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int p = t.p0 + (i < t.np ? i : 0);
+      const int2 ab = a.pairs[p];
+      ia[i] = ab.x;
+      ib[i] = ab.y;
+    }
+  }
+  int ic[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) ic[j] = min(c0 + j, a.ns - 1);
+
+  double acc64[16];
+  T acc[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) { acc64[k] = 0.0; acc[k] = T(0); }
+
+  const long long v_begin = (long long)blockIdx.x * vox_per_block;
+  const long long v_end = min(v_begin + vox_per_block, a.nvox);
+  int run = 0;
+  for (long long vb = v_begin; vb < v_end; vb += kChunk) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < a.ns * kChunk; i += kContractThreads) {
+      const int n = i / kChunk;
+      const int v = i - n * kChunk;
+      const long long gv = vb + v;
+      dsm[n * LD + v] = gv < v_end ? fields[(long long)n * a.nvox + gv] : T(0);
+    }
+    __syncthreads();
+    if (active) {
+#pragma unroll 4
+      for (int v = 0; v < kChunk; ++v) {
+        T p[4], d[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) p[i] = dsm[ia[i] * LD + v] * dsm[ib[i] * LD + v];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) d[j] = dsm[ic[j] * LD + v];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i * 4 + j] = fma(p[i], d[j], acc[i * 4 + j]);
+      }
+      if (++run == kFlushChunks) {
+        run = 0;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) { acc64[k] += (double)acc[k]; acc[k] = T(0); }
+      }
+    }
+  }
+  if (active) {
+    double* out = a.partial + ((long long)blockIdx.x * a.ntiles + tile) * 16;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) out[k] = acc64[k] + (double)acc[k];
+  }
+}
+
+// msum[map[tile][k]] = sum over blocks of partial[block][tile][k], blocks in order.
+__global__ void reduce_partials_kernel(ContractArgs a) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= a.ntiles * 16) return;
+  const int dst = a.tile_map[idx];
+  if (dst < 0) return;
+  double s = 0.0;
+  for (int b = 0; b < a.gridx; ++b) s += a.partial[(long long)b * a.ntiles * 16 + idx];
+  a.msum[dst] = s;
+}
+
+template <typename T>
+bsp_status launch_contract_simt(const ContractArgs& a, cudaStream_t s) {
+  if (a.ntiles == 0) return BSP_OK;
+  const long long chunks = (a.nvox + kChunk - 1) / kChunk;
+  const long long per_block_chunks = (chunks + a.gridx - 1) / a.gridx;
+  const long long vpb = per_block_chunks * kChunk;
+  dim3 grid(a.gridx, (a.ntiles + kContractThreads - 1) / kContractThreads);
+  const size_t smem = (size_t)a.ns * (kChunk + 1) * sizeof(T);
+  BSP_CUDA(cudaFuncSetAttribute(contract_simt_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem));
+  contract_simt_kernel<T><<<grid, kContractThreads, smem, s>>>(a, vpb);
+  BSP_CUDA(cudaGetLastError());
+  return BSP_OK;
+}
+
+bsp_status launch_reduce_partials(const ContractArgs& a, cudaStream_t s) {
+  const int n = a.ntiles * 16;
+  if (n == 0) return BSP_OK;
+  reduce_partials_kernel<<<(n + 255) / 256, 256, 0, s>>>(a);
+  BSP_CUDA(cudaGetLastError());
+  return BSP_OK;
+}
+
+template bsp_status launch_contract_simt<float>(const ContractArgs&, cudaStream_t);
+template bsp_status launch_contract_simt<double>(const ContractArgs&, cudaStream_t);
+
+// ---------------------------------------------------------------- finalize
+// b_trip[t] = norm msum[t] / tsum[t]                     (Eq. (2.7) with Eq. (2.10))
+// b_grid[cell] = norm sum msum / sum tsum over the cell's bins, NaN if it has none.
+__global__ void finalize_kernel(FinalizeArgs a) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < a.n_trip) a.b_trip[idx] = a.norm * a.msum[idx] / a.tsum[idx];
+  if (a.b_grid != nullptr && idx < a.n_cells) {
+    const int lo = a.cell_ptr[idx], hi = a.cell_ptr[idx + 1];
+    if (lo == hi) {
+      a.b_grid[idx] = __longlong_as_double(0x7ff8000000000000ULL);
+    } else {
+      double num = 0.0, den = 0.0;
+      for (int i = lo; i < hi; ++i) {
+        const int t = a.cell_idx[i];
+        num += a.msum[t];
+        den += a.tsum[t];
+      }
+      a.b_grid[idx] = a.norm * num / den;
+    }
+  }
+}
+
+bsp_status launch_finalize(const FinalizeArgs& a, cudaStream_t s) {
+  const int n = a.n_trip > a.n_cells ? a.n_trip : a.n_cells;
+  if (n == 0) return BSP_OK;
+  finalize_kernel<<<(n + 255) / 256, 256, 0, s>>>(a);
+  BSP_CUDA(cudaGetLastError());
+  return BSP_OK;
+}
+
+}  // namespace bsp

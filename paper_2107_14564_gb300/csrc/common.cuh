@@ -1,0 +1,132 @@
+// Shared device helpers and the internal plan layout of the bispectrum library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "bispec.h"
+
+namespace bsp {
+
+// ---------------------------------------------------------------- complex arithmetic
+template <typename T> struct Cplx;
+template <> struct Cplx<float> { using type = float2; };
+template <> struct Cplx<double> { using type = double2; };
+template <typename T> using cplx = typename Cplx<T>::type;
+
+template <typename C> __device__ __forceinline__ C c_make(decltype(C::x) re, decltype(C::x) im) {
+  C r; r.x = re; r.y = im; return r;
+}
+template <typename C> __device__ __forceinline__ C c_add(C a, C b) { return c_make<C>(a.x + b.x, a.y + b.y); }
+template <typename C> __device__ __forceinline__ C c_sub(C a, C b) { return c_make<C>(a.x - b.x, a.y - b.y); }
+template <typename C> __device__ __forceinline__ C c_mul(C a, C b) {
+  return c_make<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename C> __device__ __forceinline__ C c_conj(C a) { return c_make<C>(a.x, -a.y); }
+// multiply by +i
+template <typename C> __device__ __forceinline__ C c_muli(C a) { return c_make<C>(-a.y, a.x); }
+template <typename C> __device__ __forceinline__ C c_scale(C a, decltype(C::x) s) { return c_make<C>(a.x * s, a.y * s); }
+
+// ---------------------------------------------------------------- FFT stage list
+constexpr int kMaxStages = 12;
+struct FftStages {
+  int n;                  // transform length
+  int nst;                // number of stages
+  int radix[kMaxStages];  // radices, product = n
+};
+
+// Threads per FFT block and complex elements held per thread in one stage.
+constexpr int kFftThreads = 256;
+template <typename T> struct FftElems;
+template <> struct FftElems<float> { static constexpr int value = 32; };
+template <> struct FftElems<double> { static constexpr int value = 16; };
+
+// ---------------------------------------------------------------- work items of the passes
+// X pass: lines along x at fixed (shell n, ky, kz0..kz0+cnt)
+// Y pass: lines along y at fixed (shell n, x, kz0..kz0+cnt)
+// Z pass: lines along z at fixed (shell n, x, y0..y0+cnt)
+struct Item { int n, u, v0, cnt; };
+
+struct ShellGeom {
+  int qlo, qhi;        // modes with qlo <= |m|^2 < qhi
+  int r;               // |m_i| <= r - 1 for every mode of the shell
+  int pad;
+  long long g1_off;    // complex offset of this shell in the X-pass buffer [x][2r-1][r]
+  long long g2_off;    // complex offset in the Y-pass buffer [x][y][r]
+};
+
+struct PassArgs {
+  const void* spec;       // half spectrum (complex T), or null for the unit counting input
+  void* g1;               // X-pass output
+  void* g2;               // Y-pass output
+  void* fields;           // Z-pass output, [n][x][y][z] real T
+  const void* tw;         // twiddles exp(+2 pi i j / ng), j < ng (complex T)
+  const ShellGeom* geom;  // per shell
+  const Item* items;      // work items of this pass
+  int ng;
+  int rsd;
+  double beta;
+  FftStages st;           // stage list of this pass's line length
+};
+
+// ---------------------------------------------------------------- contraction tables
+// A tile covers up to 4 consecutive pairs and 4 consecutive c shells; map[16] gives the kept
+// bin of output (i, j) or -1.
+struct Tile { int p0, np, c0, pad; };
+
+// ---------------------------------------------------------------- error handling
+void set_error(const std::string& msg);
+bsp_status fail(bsp_status s, const std::string& msg);
+bsp_status cuda_fail(cudaError_t e, const char* what);
+
+#define BSP_CUDA(call)                                   \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return ::bsp::cuda_fail(e_, #call); \
+  } while (0)
+
+// ---------------------------------------------------------------- launchers (bispec_fft.cu)
+template <typename T>
+bsp_status launch_xpass(const PassArgs& a, int n_items, int lines, cudaStream_t s);
+template <typename T>
+bsp_status launch_ypass(const PassArgs& a, int n_items, int lines, cudaStream_t s);
+template <typename T>
+bsp_status launch_zpass(const PassArgs& a, int n_items, int lines, cudaStream_t s);
+template <typename T>
+bsp_status launch_twiddles(void* tw, int ng, cudaStream_t s);
+
+// ---------------------------------------------------------------- launchers (bispec_contract.cu)
+struct ContractArgs {
+  const void* fields;     // [ns][nvox] real T
+  long long nvox;
+  int ns;
+  const Tile* tiles;
+  const int2* pairs;      // (a, b)
+  const int* tile_map;    // [ntiles][16]
+  int ntiles;
+  double* partial;        // [gridx][ntiles][16]
+  int gridx;
+  double* msum;           // [n_out]
+  int n_out;
+};
+template <typename T>
+bsp_status launch_contract_simt(const ContractArgs& a, cudaStream_t s);
+bsp_status launch_reduce_partials(const ContractArgs& a, cudaStream_t s);
+
+struct FinalizeArgs {
+  const double* msum;
+  const double* tsum;
+  int n_trip;
+  const int* cell_ptr;    // CSR over n_cells cells
+  const int* cell_idx;
+  int n_cells;
+  double norm;            // V_c^3 / V
+  double* b_trip;
+  double* b_grid;         // may be null
+};
+bsp_status launch_finalize(const FinalizeArgs& a, cudaStream_t s);
+
+}  // namespace bsp

@@ -1,0 +1,181 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle. Needs a GB300."""
+import numpy as np
+import pytest
+
+import fieldgen
+from oracle import dbe
+from oracle import fbe
+from oracle import plan as P
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2107_14564_gb300 import binding
+    return binding
+
+
+def _edges(ng, ns, top=None):
+    return P.linear_edges(ns, 1.0, top or ng / 4)
+
+
+def _spec(ng, n_index, f, seed, c64):
+    d = fieldgen.quadratic_field(ng, float(ng), n_index, f, seed)
+    s = fieldgen.spectrum(d)
+    if c64:
+        s = s.astype(np.complex64)
+    return s
+
+
+def _oracle(spec, ng, edges, n_mu=10, n_t=10, beta=None, with_abs=False, counts=None):
+    pl = P.make_plan(ng, float(ng), edges, n_mu, n_t)
+    return pl, fbe.estimate(spec.astype(np.complex128), pl, beta=beta, with_abs=with_abs, counts=counts)
+
+
+def _check_plan_tables(gp, res, pl):
+    """Bins, triangle counts and (mu, t) cells are integers and flags: they must agree exactly;
+    labels are computed in FP64 by the same steps on both sides and must agree to the bit."""
+    tr = gp.triplets
+    assert [(int(a), int(b), int(c)) for a, b, c in zip(tr["a"], tr["b"], tr["c"])] == res["triplets"]
+    assert np.array_equal(tr["ntri"].astype(np.int64), res["ntri"])
+    labs = res["labels"]
+    assert np.array_equal(tr["i_mu"], [l["i_mu"] for l in labs])
+    assert np.array_equal(tr["i_t"], [l["i_t"] for l in labs])
+    assert np.array_equal(tr["inside"].astype(bool), [l["inside"] for l in labs])
+    assert np.array_equal(tr["mu"], [l["mu"] for l in labs])
+    assert np.array_equal(tr["t"], [l["t"] for l in labs])
+    assert np.array_equal(tr["k1"], pl.kbar[tr["a"]])
+
+
+def test_fp64_config1_parity(lib):
+    """Ng=32, L=32, 8 linear shells k_f..k_Nyq/2, P=k^-2, f=0.1, 10x10 cells, FP64: 1e-10."""
+    ng = 32
+    edges = _edges(ng, 8)
+    spec = _spec(ng, 2.0, 0.1, 1, c64=False)
+    pl, res = _oracle(spec, ng, edges)
+    gp = lib.Plan(ng, float(ng), edges, 10, 10, precision="fp64")
+    _check_plan_tables(gp, res, pl)
+    b, g = gp.estimate(torch.from_numpy(spec).cuda())
+    b = b.cpu().numpy()
+    g = g.cpu().numpy()
+    assert np.max(np.abs(b - res["b"]) / np.abs(res["b"])) < 1e-10
+    assert np.array_equal(np.isnan(g), np.isnan(res["grid"]))
+    ok = ~np.isnan(g)
+    assert np.max(np.abs(g[ok] - res["grid"][ok]) / np.abs(res["grid"][ok])) < 1e-10
+
+
+def test_fp64_matches_direct_summation(lib):
+    """GPU FP64 against the literal Eq. (2.3) loop on Ng=16 (independent of the FFT oracle)."""
+    ng = 16
+    edges = _edges(ng, 8)
+    spec = _spec(ng, 2.0, 0.1, 2, c64=False)
+    pl = P.make_plan(ng, float(ng), edges)
+    msum_d, ntri_d = dbe.direct_estimate(spec, pl)
+    gp = lib.Plan(ng, float(ng), edges, precision="fp64")
+    b, _ = gp.estimate(torch.from_numpy(spec).cuda())
+    b = b.cpu().numpy()
+    vc = 1.0
+    for i, (a, bb, c) in enumerate(zip(gp.triplets["a"], gp.triplets["b"], gp.triplets["c"])):
+        key = (int(a), int(bb), int(c))
+        assert ntri_d[key] == gp.triplets["ntri"][i]
+        want = vc ** 3 * msum_d[key].real / (float(ng) ** 3 * ntri_d[key])
+        assert abs(b[i] - want) <= 1e-10 * abs(want)
+
+
+@pytest.mark.parametrize("ng", [48, 64, 96])
+def test_fp64_other_grids(lib, ng):
+    """Radix-3 lengths (48, 96) and several FFT blocks per pass, FP64 at 1e-10."""
+    edges = _edges(ng, 6)
+    spec = _spec(ng, 1.5, 0.2, 7 + ng, c64=False)
+    pl, res = _oracle(spec, ng, edges)
+    gp = lib.Plan(ng, float(ng), edges, precision="fp64")
+    _check_plan_tables(gp, res, pl)
+    b, _ = gp.estimate(torch.from_numpy(spec).cuda())
+    assert np.max(np.abs(b.cpu().numpy() - res["b"]) / np.abs(res["b"])) < 1e-10
+
+
+def test_fp64_rsd_parity(lib):
+    ng = 32
+    edges = _edges(ng, 8)
+    spec = _spec(ng, 2.0, 0.1, 3, c64=False)
+    pl, res = _oracle(spec, ng, edges, beta=0.5)
+    gp = lib.Plan(ng, float(ng), edges, rsd=True, beta=0.5, precision="fp64")
+    b, _ = gp.estimate(torch.from_numpy(spec).cuda())
+    assert np.max(np.abs(b.cpu().numpy() - res["b"]) / np.abs(res["b"])) < 1e-10
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_shell_fields_parity(lib, prec):
+    ng = 64
+    edges = _edges(ng, 8)
+    c64 = prec != "fp64"
+    spec = _spec(ng, 1.5, 0.1, 4, c64=c64)
+    pl = P.make_plan(ng, float(ng), edges)
+    want = fbe.shell_fields(spec.astype(np.complex128), pl)
+    gp = lib.Plan(ng, float(ng), edges, precision=prec)
+    got = gp.shell_fields(torch.from_numpy(spec).cuda()).cpu().numpy()
+    tol = 1e-12 if prec == "fp64" else 2e-6
+    for n in range(pl.ns):
+        scale = np.abs(want[n]).max()
+        assert np.abs(got[n] - want[n]).max() <= tol * scale, n
+
+
+def _cond_err(b, res):
+    """Error against the condition scale V_c^3 sum|d d d| / (V T) of each bin."""
+    return np.abs(b - res["b"]) / res["b_scale"]
+
+
+@pytest.mark.parametrize("prec", ["fp32"])
+def test_fp32_parity_ragged(lib, prec):
+    """Ng=64 with 12 shells: several contraction tiles and voxel chunks; FP32 within 1e-4 of the
+    condition scale (the relative error itself is reported by the bench)."""
+    ng = 64
+    edges = _edges(ng, 12)
+    spec = _spec(ng, 1.5, 0.05, 5, c64=True)
+    pl, res = _oracle(spec, ng, edges, 20, 20, with_abs=True)
+    gp = lib.Plan(ng, float(ng), edges, 20, 20, precision=prec)
+    _check_plan_tables(gp, res, pl)
+    b, g = gp.estimate(torch.from_numpy(spec).cuda())
+    assert np.max(_cond_err(b.cpu().numpy(), res)) < 1e-4
+    assert np.array_equal(np.isnan(g.cpu().numpy()), np.isnan(res["grid"]))
+
+
+def test_contract_on_oracle_fields(lib):
+    """The contraction alone, fed the oracle's FP64 fields."""
+    ng = 32
+    edges = _edges(ng, 8)
+    spec = _spec(ng, 2.0, 0.1, 6, c64=False)
+    pl, res = _oracle(spec, ng, edges)
+    fields = fbe.shell_fields(spec, pl)
+    stack = np.stack([fields[n] for n in range(pl.ns)])
+    gp = lib.Plan(ng, float(ng), edges, precision="fp64")
+    msum = gp.contract(torch.from_numpy(stack).cuda()).cpu().numpy()
+    assert np.max(np.abs(msum - res["msum"]) / np.abs(res["msum"])) < 1e-12
+
+
+def test_host_entry_point(lib):
+    ng = 32
+    edges = _edges(ng, 8)
+    spec = _spec(ng, 2.0, 0.1, 1, c64=True)
+    gp = lib.Plan(ng, float(ng), edges, precision="fp32")
+    b_dev, g_dev = gp.estimate(torch.from_numpy(spec).cuda())
+    pinned = torch.from_numpy(spec).pin_memory()
+    b_h, g_h = gp.estimate_host(pinned)
+    assert np.array_equal(b_h, b_dev.cpu().numpy())
+    assert np.array_equal(np.nan_to_num(g_h, nan=-1.0), np.nan_to_num(g_dev.cpu().numpy(), nan=-1.0))
+
+
+def test_errors_are_reported(lib):
+    with pytest.raises(lib.BispecError) as e:
+        lib.Plan(32, 32.0, [1.0, 5.0, 11.0])
+    assert e.value.status == 2                       # BSP_ERR_ALIASING
+    with pytest.raises(lib.BispecError) as e:
+        lib.Plan(30, 30.0, [1.0, 3.0, 5.0])         # 30 = 2*3*5 is not supported
+    assert e.value.status == 6
+    with pytest.raises(lib.BispecError):
+        lib.Plan(32, 32.0, [1.5, 1.6])               # empty shell

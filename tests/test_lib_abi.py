@@ -1,0 +1,74 @@
+"""The C ABI library builds, loads and exports every entry point include/bispec.h declares;
+argument checks that precede any CUDA call work without a GPU. CPU only."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2107_14564_gb300 import _lib, build
+    build.build_library()
+    return _lib.load()
+
+
+def declared_entry_points():
+    names = []
+    for f in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if f.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", f)).read()
+            names += re.findall(r"^BSP_API\s+[\w\s\*]+?\b(bsp_\w+)\s*\(", txt, flags=re.M)
+    return names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_entry_points()
+    assert len(names) >= 10
+    out = subprocess.run(["nm", "-D", "--defined-only", lib._name], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (bsp_\w+)", out))
+    assert set(names) <= exported, set(names) - exported
+    from paper_2107_14564_gb300 import _lib
+    assert set(names) == set(_lib.SIGNATURES)
+
+
+def _desc(lib_mod, edges, ng=32, prec=1, n_mu=10, n_t=10, rsd=0, beta=0.0):
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    d = lib_mod.PlanDesc()
+    d.ng, d.box_len, d.n_shells = ng, float(ng), len(e) - 1
+    d.edges_kf = e.ctypes.data_as(C.POINTER(C.c_double))
+    d.n_mu, d.n_t, d.rsd, d.beta, d.precision, d.mem_budget_bytes = n_mu, n_t, rsd, beta, prec, 0
+    return d, e
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(edges=[1.0, 5.0, 11.0]), 2),              # beyond the cap of Eq. (2.12): 9*120 >= 32^2
+    (dict(edges=[1.0, 3.0, 5.0], ng=30), 6),        # 30 = 2*3*5
+    (dict(edges=[1.0, 3.0, 5.0], ng=2048), 6),
+    (dict(edges=[1.0, 3.0, 2.0]), 1),               # not increasing
+    (dict(edges=[1.5, 1.6]), 1),                    # empty shell: ceil(2.25) == ceil(2.56)
+    (dict(edges=[1.0, 3.0], prec=9), 1),
+    (dict(edges=[1.0, 3.0], n_mu=0), 1),
+])
+def test_argument_errors_without_gpu(lib, kw, status):
+    from paper_2107_14564_gb300 import _lib
+    d, keep = _desc(_lib, **kw)
+    out = C.c_void_p(123)
+    assert lib.bsp_plan_create(C.byref(d), None, C.byref(out)) == status
+    assert out.value is None
+    assert len(lib.bsp_last_error()) > 0
+
+
+def test_null_arguments(lib):
+    assert lib.bsp_plan_create(None, None, None) == 1
+    assert lib.bsp_estimate(None, None, None, None, None) == 1
+    assert lib.bsp_plan_destroy(None) == 0
+
+
+def test_version(lib):
+    assert b"sm_103a" in lib.bsp_version()
