@@ -1,0 +1,373 @@
+#!/usr/bin/env python
+"""Throughput of the FFT bispectrum estimator on GB300 (one JSON line on stdout).
+
+A step is one full estimate (all shell FFT passes, the triple-product contraction and the
+(k1, mu, t) map) of one synthetic field already resident in device memory. The default
+workload is the Ng=512 redshift-space case: L=512, linear RSD (Kaiser, beta=0.5, line of sight
+z) on the quadratic non-Gaussian field (P(k)=k^-1.5, f_NG=0.05), 32 linear shells from k_f to
+k_Nyq/2, 20x20 (mu, t) cells per k1 shell, monopole.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision P] [--impl ours|reference]
+
+Under torchrun every rank estimates its own independently seeded field (replicas of one
+problem: weak scaling, no collective on the data path); value = bins of all ranks / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "ng512_rsd": dict(ng=512, box=512.0, n_index=1.5, f_ng=0.05, beta=0.5, ns=32, top=128.0,
+                      n_mu=20, n_t=20, seed=4,
+                      text="Ng=512 L=512 quadratic NG field P=k^-1.5 f=0.05, Kaiser RSD beta=0.5 "
+                           "(LoS z), 32 linear shells k_f..k_Nyq/2, 20x20 (mu,t) cells, monopole"),
+    "ng256": dict(ng=256, box=256.0, n_index=1.5, f_ng=0.05, beta=None, ns=24, top=64.0,
+                  n_mu=20, n_t=20, seed=3,
+                  text="Ng=256 L=256 quadratic NG field P=k^-1.5 f=0.05, 24 linear shells "
+                       "k_f..k_Nyq/2, 20x20 (mu,t) cells"),
+}
+DTYPES = {"fp64": "f64", "fp32": "f32", "mixed_bf16x3": "bf16x3/f32"}
+STAGES = ["xpass", "ypass", "zpass", "contract", "finalize"]
+STAGE_KERNEL_SRC = {"xpass": "bispec_fft.cu", "ypass": "bispec_fft.cu", "zpass": "bispec_fft.cu",
+                    "contract": "bispec_contract.cu", "finalize": "bispec_contract.cu"}
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+def src_hash(name):
+    path = os.path.join(ROOT, "paper_2107_14564_gb300", "csrc", name)
+    with open(path, "rb") as fh:
+        return hashlib.sha1(fh.read()).hexdigest()[:12]
+
+
+def ncu_traffic(stage, workload, precision):
+    """DRAM bytes per launch of the stage's kernel from the committed ncu summary, or None when
+    the kernel source changed since the capture."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            tab = json.load(fh)
+    except OSError:
+        return None
+    e = tab.get(f"{workload}/{precision}/{stage}")
+    if not e or e.get("src_sha1") != src_hash(STAGE_KERNEL_SRC[stage]):
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in self.rows if len(r) >= 9 for n, v in zip(names, r[5:9])
+                          if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(sm)}
+
+
+def make_input(w, seed):
+    import fieldgen
+    delta = fieldgen.quadratic_field(w["ng"], w["box"], w["n_index"], w["f_ng"], seed)
+    return fieldgen.half_spectrum_c64(delta)
+
+
+def edges_of(w):
+    import numpy as np
+    return np.linspace(1.0, w["top"], w["ns"] + 1)
+
+
+# ------------------------------------------------------------------ CPU oracle baseline
+def oracle_sample(w, spec_c64, n_triplets, n_pairs):
+    """Time the FP64 oracle on a bounded sample of the workload and extrapolate to one full
+    estimate: ns shell FFTs (with the RSD factor), n_pairs pair products, n_triplets dot
+    products. Returns (bins/s, seconds of the sample, description)."""
+    import numpy as np
+    from oracle import fbe
+    from oracle import plan as P
+    pl = P.make_plan(w["ng"], w["box"], edges_of(w), w["n_mu"], w["n_t"])
+    spec = spec_c64.astype(np.complex128)
+    t0 = time.perf_counter()
+    if w["beta"] is not None:
+        spec = spec * fbe.kaiser_factor_half(w["ng"], w["beta"])
+    f = fbe.shell_fields(spec, pl, shells=[w["ns"] - 1, w["ns"] - 2])
+    t1 = time.perf_counter()
+    t_fft = (t1 - t0) / 2
+    a, b = w["ns"] - 1, w["ns"] - 2
+    t1 = time.perf_counter()
+    prod = (f[a] * f[b]).ravel()
+    t2 = time.perf_counter()
+    mat = np.stack([f[a].ravel(), f[b].ravel()])
+    t3 = time.perf_counter()
+    for _ in range(4):
+        mat @ prod
+    t4 = time.perf_counter()
+    t_pair = t2 - t1
+    t_dot = (t4 - t3) / 8
+    total = w["ns"] * t_fft + n_pairs * t_pair + n_triplets * t_dot
+    desc = (f"oracle timed on 2 of {w['ns']} shell FFTs, 1 of {n_pairs} pair products and 8 of "
+            f"{n_triplets} triple-product sums at full Ng={w['ng']}, extrapolated to one estimate "
+            f"({total:.1f} s)")
+    return n_triplets / total, t4 - t0, desc
+
+
+def run_reference(args, w):
+    """Reference arm: the FP64 CPU oracle on the same workload, metric and unit."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import fbe
+    from oracle import plan as P
+    spec = make_input(w, w["seed"])
+    pl = P.make_plan(w["ng"], w["box"], edges_of(w), w["n_mu"], w["n_t"])
+    # bin list from the data-independent counts (plan time, excluded as in the GPU arm)
+    n_trip, n_pairs = gpu_free_bin_counts(pl)
+    for _ in range(args.warmup):
+        pass
+    vals = []
+    t_all = time.perf_counter()
+    for _ in range(args.steps):
+        v, _, desc = oracle_sample(w, spec, n_trip, n_pairs)
+        vals.append(v)
+    elapsed = time.perf_counter() - t_all
+    value = statistics.mean(vals)
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": metric_name(w), "value": value, "unit": "bins/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * elapsed / max(args.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(w, "fp64"),
+            "cpu_baseline": {"value": value, "unit": "bins/s", "cores": cores, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": "bins/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def gpu_free_bin_counts(pl):
+    """(kept bins, distinct pairs) from the oracle's own counting fields at this size is too slow
+    for a bench step; the counts come from the CUDA plan when it exists, else from the triangle
+    inequality (an upper bound), which is what the reference arm uses."""
+    from oracle import plan as P
+    trips = pl.candidates
+    pairs = {(a, b) for a, b, _ in trips}
+    return len(trips), len(pairs)
+
+
+def metric_name(w):
+    return f"triangle bins/sec at Ng={w['ng']} (all (k1,mu,t) bins)"
+
+
+def config_of(w, precision):
+    return {"workload": w["text"], "ng": w["ng"], "box_len": w["box"], "n_shells": w["ns"],
+            "n_mu": w["n_mu"], "n_t": w["n_t"], "rsd_beta": w["beta"], "precision": precision,
+            "l2": "inputs larger than L2 (spectrum 0.54 GB, shell fields >16 GB per step)"}
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_ours(args, w):
+    import numpy as np
+    import torch
+    from paper_2107_14564_gb300 import _lib, binding
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    spec_np = make_input(w, w["seed"] + 1000 * rank)
+    spec = torch.from_numpy(spec_np).cuda()
+    t0 = time.perf_counter()
+    plan = binding.Plan(w["ng"], w["box"], edges_of(w), w["n_mu"], w["n_t"],
+                        rsd=w["beta"] is not None, beta=w["beta"] or 0.0, precision=args.precision)
+    plan_s = time.perf_counter() - t0
+    log(f"[bench] plan: {plan.n_triplets} bins, {plan.device_bytes / 1e9:.1f} GB on device, "
+        f"{plan_s:.1f} s")
+    for _ in range(args.warmup):
+        plan.estimate(spec)
+    torch.cuda.synchronize()
+    lib = _lib.load()
+    _lib.check(lib.bsp_timing_enable(plan.handle, 1, args.steps))
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.estimate(spec)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    import ctypes as C
+    st_ms = (C.c_double * 5)()
+    ncalls = C.c_int()
+    nlaunch = C.c_longlong()
+    _lib.check(lib.bsp_timing_read(plan.handle, st_ms, C.byref(ncalls), C.byref(nlaunch)))
+    _lib.check(lib.bsp_timing_enable(plan.handle, 0, 0))
+    wb = (C.c_double * 5)()
+    wf = (C.c_double * 5)()
+    _lib.check(lib.bsp_plan_stage_work(plan.handle, wb, wf))
+    ms_max = ms
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    bins = plan.n_triplets * world
+    value = bins / (ms_max / 1000.0)
+    fields_per_s = plan.n_shells * world / (ms_max / 1000.0)
+
+    # end to end through the host-buffer entry point
+    pinned = torch.from_numpy(spec_np).pin_memory()
+    plan.estimate_host(pinned)
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        plan.estimate_host(pinned)
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": bins / e2e_s, "unit": "bins/s",
+           "h2d_bytes_per_step": int(spec_np.nbytes),
+           "d2h_bytes_per_step": int(8 * (plan.n_triplets + plan.n_shells * w["n_mu"] * w["n_t"]))}
+
+    pk, pk_kind = peaks()
+    stages = {}
+    for i, name in enumerate(STAGES):
+        t = st_ms[i] / 1000.0
+        d = {"ms": round(st_ms[i], 4), "algo_bytes": wb[i], "algo_flops": wf[i]}
+        if t > 0:
+            d["gbs"] = round(wb[i] / t / 1e9, 1)
+            d["hbm_frac"] = round(wb[i] / t / 1e9 / pk["hbm_gbs"], 3)
+            if wf[i] > 0:
+                d["tflops"] = round(wf[i] / t / 1e12, 2)
+        stages[name] = d
+    dom = max(range(5), key=lambda i: st_ms[i])
+    dname = STAGES[dom]
+    tdom = st_ms[dom] / 1000.0
+    if dname == "contract" and args.precision == "fp32":
+        sm_mhz = pk.get("sm_max_mhz", 2070.0)
+        alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+        ach = wf[dom] / tdom / 1e12
+        roof = {"bound": "alu", "kernel": "contract_simt_kernel<float>", "achieved": round(ach, 2),
+                "peak": round(alu_peak, 1), "unit": "TFLOP/s", "frac": round(ach / alu_peak, 4),
+                "peak_kind": f"FP32 CUDA-core FMA, 152 SM x 128 lanes x 2 x {sm_mhz:.0f} MHz",
+                "traffic": ncu_traffic(dname, args.workload, args.precision)}
+    else:
+        ach = wb[dom] / tdom / 1e9
+        roof = {"bound": "hbm", "kernel": dname, "achieved": round(ach, 1), "peak": pk["hbm_gbs"],
+                "unit": "GB/s", "frac": round(ach / pk["hbm_gbs"], 4),
+                "peak_kind": f"{pk_kind} hbm_gbs",
+                "traffic": ncu_traffic(dname, args.workload, args.precision)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        tr = plan.triplets
+        npairs = len({(int(a), int(b)) for a, b in zip(tr["a"], tr["b"])})
+        v, secs, desc = oracle_sample(w, spec_np, plan.n_triplets, npairs)
+        cpu = {"value": v, "unit": "bins/s", "cores": os.cpu_count(), "kind": "oracle", "sample": desc}
+
+    line = {"metric": metric_name(w), "value": value, "unit": "bins/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": DTYPES[args.precision], "data": "synthetic", "config": config_of(w, args.precision),
+            "fields_per_sec": fields_per_s, "n_bins": plan.n_triplets, "roofline": roof,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(nlaunch.value), "clocks": clk,
+            "stages": stages, "plan_seconds": round(plan_s, 2)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp32", "mixed_bf16x3", "fp64"], default="fp32")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="ng512_rsd")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        log("[bench] warmup raised to 3")
+        args.warmup = 3
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, w)
+    else:
+        run_ours(args, w)
+
+
+if __name__ == "__main__":
+    main()

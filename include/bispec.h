@@ -137,6 +137,31 @@ BSP_API bsp_status bsp_estimate_host(bsp_plan* plan, const void* spec_host, doub
  * device pointer owned by the plan (n_triplets doubles, valid until the next call on it). */
 BSP_API bsp_status bsp_last_sums(const bsp_plan* plan, const double** msum);
 
+/* Stages of one bsp_estimate, in launch order (for bsp_timing_read and bsp_plan_stage_work). */
+enum {
+  BSP_STAGE_XPASS = 0,    /* shell-masked C2C along x (Eq. (2.8)) */
+  BSP_STAGE_YPASS = 1,    /* C2C along y */
+  BSP_STAGE_ZPASS = 2,    /* C2R along z: the shell fields d_n(x) */
+  BSP_STAGE_CONTRACT = 3, /* triple products sum_x d_a d_b d_c (Eq. (2.7) numerator) */
+  BSP_STAGE_FINALIZE = 4, /* cross-block sums, B = V_c^3 M / (V T) and the (mu, t) cells */
+  BSP_N_STAGES = 5
+};
+
+/* Start (enable=1) or stop (0) per-stage timing of bsp_estimate on this plan. While enabled,
+ * each bsp_estimate records CUDA events between its stages on the call's stream, for at most
+ * `max_calls` calls after the last enable (the events are created here, not during the calls).
+ * Enabling resets the accumulated times. Errors: BSP_ERR_INVALID_ARG, BSP_ERR_CUDA. */
+BSP_API bsp_status bsp_timing_enable(bsp_plan* plan, int enable, int max_calls);
+
+/* Average milliseconds per recorded call of each stage (ms[BSP_N_STAGES]), the number of
+ * recorded calls and the number of kernels those calls launched. Waits for the recorded events. */
+BSP_API bsp_status bsp_timing_read(bsp_plan* plan, double* ms, int* n_calls, long long* n_launches);
+
+/* Algorithmic work of one bsp_estimate per stage: bytes[s] that stage must move to or from
+ * device memory (reads of the non-zero inputs it needs plus its outputs, each once) and
+ * flops[s] of its arithmetic core (0 where it is negligible). Host-side, no GPU work. */
+BSP_API bsp_status bsp_plan_stage_work(const bsp_plan* plan, double* bytes, double* flops);
+
 /* Message of the last failing call on this thread ("" if none). */
 BSP_API const char* bsp_last_error(void);
 

@@ -89,6 +89,12 @@ struct bsp_plan {
   double* tsum = nullptr;
   int* cell_ptr = nullptr;
   int* cell_idx = nullptr;
+  // per-stage timing (bsp_timing_enable)
+  bool timing_on = false;
+  int timing_max = 0;
+  int timing_calls = 0;
+  std::vector<cudaEvent_t> events;   // timing_max x (BSP_N_STAGES + 1)
+  long long launches = 0;            // kernels launched by recorded calls
   // host staging for bsp_estimate_host
   void* spec_dev = nullptr;
   double* btrip_dev = nullptr;
@@ -397,9 +403,33 @@ bsp_status count_triangles(bsp_plan* p, const std::vector<int>& ca, const std::v
 
 template <typename T>
 bsp_status estimate_impl(bsp_plan* p, const void* spec, double* b_trip, double* b_grid, cudaStream_t s) {
-  bsp_status st = run_passes<T>(p, spec, p->rsd, p->tw, p->g1, p->g2, p->fields, p->d_xi, p->nxi,
-                                p->d_yi, p->nyi, p->d_zi, p->nzi, p->lines_xy, p->lines_z, s);
+  const bool rec = p->timing_on && p->timing_calls < p->timing_max;
+  cudaEvent_t* ev = rec ? &p->events[(size_t)p->timing_calls * (BSP_N_STAGES + 1)] : nullptr;
+  if (rec) BSP_CUDA(cudaEventRecord(ev[0], s));
+  PassArgs a{};
+  a.spec = spec;
+  a.g1 = p->g1;
+  a.g2 = p->g2;
+  a.fields = p->fields;
+  a.tw = p->tw;
+  a.geom = p->d_geom;
+  a.ng = p->ng;
+  a.rsd = p->rsd;
+  a.beta = p->beta;
+  a.st = p->st_full;
+  a.items = p->d_xi;
+  bsp_status st = launch_xpass<T>(a, p->nxi, p->lines_xy, s);
   if (st != BSP_OK) return st;
+  if (rec) BSP_CUDA(cudaEventRecord(ev[1], s));
+  a.items = p->d_yi;
+  st = launch_ypass<T>(a, p->nyi, p->lines_xy, s);
+  if (st != BSP_OK) return st;
+  if (rec) BSP_CUDA(cudaEventRecord(ev[2], s));
+  a.items = p->d_zi;
+  a.st = p->st_half;
+  st = launch_zpass<T>(a, p->nzi, p->lines_z, s);
+  if (st != BSP_OK) return st;
+  if (rec) BSP_CUDA(cudaEventRecord(ev[3], s));
   ContractArgs c{};
   c.fields = p->fields;
   c.nvox = p->nvox();
@@ -414,6 +444,7 @@ bsp_status estimate_impl(bsp_plan* p, const void* spec, double* b_trip, double* 
   c.n_out = (int)p->trips.size();
   st = launch_contract_simt<T>(c, s);
   if (st != BSP_OK) return st;
+  if (rec) BSP_CUDA(cudaEventRecord(ev[4], s));
   st = launch_reduce_partials(c, s);
   if (st != BSP_OK) return st;
   FinalizeArgs f{};
@@ -427,7 +458,47 @@ bsp_status estimate_impl(bsp_plan* p, const void* spec, double* b_trip, double* 
   f.norm = vc * vc * vc / (p->box_len * p->box_len * p->box_len);
   f.b_trip = b_trip;
   f.b_grid = b_grid;
-  return launch_finalize(f, s);
+  st = launch_finalize(f, s);
+  if (st != BSP_OK) return st;
+  if (rec) {
+    BSP_CUDA(cudaEventRecord(ev[5], s));
+    p->timing_calls += 1;
+    p->launches += (p->nxi > 0) + (p->nyi > 0) + (p->nzi > 0) + 2 * (p->ntiles > 0) + 1;
+  }
+  return BSP_OK;
+}
+
+// Algorithmic bytes and flops of each stage of one estimate (see bsp_plan_stage_work).
+void stage_work(const bsp_plan* p, double* bytes, double* flops) {
+  const double ce = 2.0 * p->elem();
+  const double re = (double)p->elem();
+  const double ng = (double)p->ng;
+  for (int i = 0; i < BSP_N_STAGES; ++i) { bytes[i] = 0.0; flops[i] = 0.0; }
+  for (int n = 0; n < p->ns; ++n) {
+    const ShellGeom& g = p->geom[n];
+    const int r = g.r;
+    long long modes_half = 0, xlines = 0;
+    for (int ky = -(r - 1); ky <= r - 1; ++ky)
+      for (int kz = 0; kz < r; ++kz) {
+        const long long q2 = (long long)ky * ky + (long long)kz * kz;
+        if (q2 >= g.qhi) continue;
+        xlines += 1;
+        for (int kx = -(r - 1); kx <= r - 1; ++kx) {
+          const long long q = q2 + (long long)kx * kx;
+          if (q >= g.qlo && q < g.qhi) modes_half += 1;
+        }
+      }
+    bytes[BSP_STAGE_XPASS] += ce * (double)modes_half + ce * ng * (double)xlines;
+    bytes[BSP_STAGE_YPASS] += ce * ng * (double)xlines + ce * ng * ng * r;
+    bytes[BSP_STAGE_ZPASS] += ce * ng * ng * r + re * ng * ng * ng;
+  }
+  // pairs of the kept bins
+  long long npairs = 0;
+  for (size_t t = 0; t < p->trips.size(); ++t)
+    if (t == 0 || p->trips[t].a != p->trips[t - 1].a || p->trips[t].b != p->trips[t - 1].b) npairs += 1;
+  bytes[BSP_STAGE_CONTRACT] = re * (double)p->ns * ng * ng * ng;
+  flops[BSP_STAGE_CONTRACT] = ((double)npairs + 2.0 * (double)p->trips.size()) * ng * ng * ng;
+  bytes[BSP_STAGE_FINALIZE] = 8.0 * (double)p->trips.size() * 3 + 8.0 * p->n_cells();
 }
 
 }  // namespace
@@ -553,6 +624,8 @@ bsp_status bsp_plan_create(const bsp_plan_desc* desc, void* stream, bsp_plan** o
 bsp_status bsp_plan_destroy(bsp_plan* p) {
   if (!p) return BSP_OK;
   cudaDeviceSynchronize();
+  for (cudaEvent_t e : p->events) cudaEventDestroy(e);
+  p->events.clear();
   for (auto& b : p->bufs) cudaFree(b.p);
   p->bufs.clear();
   delete p;
@@ -638,6 +711,48 @@ bsp_status bsp_estimate_host(bsp_plan* p, const void* spec_host, double* b_tripl
     BSP_CUDA(cudaMemcpyAsync(b_grid_host, p->bgrid_dev, (size_t)p->n_cells() * sizeof(double),
                              cudaMemcpyDeviceToHost, s));
   BSP_CUDA(cudaStreamSynchronize(s));
+  return BSP_OK;
+}
+
+bsp_status bsp_timing_enable(bsp_plan* p, int enable, int max_calls) {
+  if (!p || max_calls < 0) return fail(BSP_ERR_INVALID_ARG, "bad argument");
+  p->timing_on = false;
+  p->timing_calls = 0;
+  p->launches = 0;
+  if (!enable) return BSP_OK;
+  const size_t need = (size_t)max_calls * (BSP_N_STAGES + 1);
+  while (p->events.size() < need) {
+    cudaEvent_t e;
+    BSP_CUDA(cudaEventCreate(&e));
+    p->events.push_back(e);
+  }
+  p->timing_max = max_calls;
+  p->timing_on = true;
+  return BSP_OK;
+}
+
+bsp_status bsp_timing_read(bsp_plan* p, double* ms, int* n_calls, long long* n_launches) {
+  if (!p || !ms) return fail(BSP_ERR_INVALID_ARG, "NULL argument");
+  for (int i = 0; i < BSP_N_STAGES; ++i) ms[i] = 0.0;
+  for (int c = 0; c < p->timing_calls; ++c) {
+    cudaEvent_t* ev = &p->events[(size_t)c * (BSP_N_STAGES + 1)];
+    BSP_CUDA(cudaEventSynchronize(ev[BSP_N_STAGES]));
+    for (int i = 0; i < BSP_N_STAGES; ++i) {
+      float t = 0.f;
+      BSP_CUDA(cudaEventElapsedTime(&t, ev[i], ev[i + 1]));
+      ms[i] += t;
+    }
+  }
+  if (p->timing_calls > 0)
+    for (int i = 0; i < BSP_N_STAGES; ++i) ms[i] /= p->timing_calls;
+  if (n_calls) *n_calls = p->timing_calls;
+  if (n_launches) *n_launches = p->launches;
+  return BSP_OK;
+}
+
+bsp_status bsp_plan_stage_work(const bsp_plan* p, double* bytes, double* flops) {
+  if (!p || !bytes || !flops) return fail(BSP_ERR_INVALID_ARG, "NULL argument");
+  stage_work(p, bytes, flops);
   return BSP_OK;
 }
 
