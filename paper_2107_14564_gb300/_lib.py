@@ -49,6 +49,10 @@ SIGNATURES = {
     "bsp_estimate": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "bsp_estimate_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "bsp_last_sums": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p)]),
+    "bsp_timing_enable": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "bsp_timing_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int),
+                                  C.POINTER(C.c_longlong)]),
+    "bsp_plan_stage_work": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "bsp_last_error": (C.c_char_p, []),
     "bsp_version": (C.c_char_p, []),
 }

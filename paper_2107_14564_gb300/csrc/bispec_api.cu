@@ -1,6 +1,7 @@
 // C ABI of the bispectrum library: plan construction (Sec. 2.1 binning, Eq. (2.10) counts),
 // the estimator (Eqs. (2.7)-(2.11)) and the (mu, t) map (Eq. (2.4)).
 #include <math.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
@@ -11,17 +12,30 @@
 
 namespace bsp {
 
-static thread_local std::string g_error;
+// Message of the last failing call on this thread, in a fixed buffer (setting it never
+// allocates, so allocation-free entry points can report errors too).
+static thread_local char g_error[512];
 
-void set_error(const std::string& msg) { g_error = msg; }
+void set_error_c(const char* msg) {
+  size_t n = 0;
+  while (msg[n] != 0 && n + 1 < sizeof(g_error)) { g_error[n] = msg[n]; ++n; }
+  g_error[n] = 0;
+}
+
+void set_error(const std::string& msg) { set_error_c(msg.c_str()); }
 
 bsp_status fail(bsp_status s, const std::string& msg) {
-  g_error = msg;
+  set_error_c(msg.c_str());
+  return s;
+}
+
+bsp_status fail_c(bsp_status s, const char* msg) {
+  set_error_c(msg);
   return s;
 }
 
 bsp_status cuda_fail(cudaError_t e, const char* what) {
-  g_error = std::string("CUDA error in ") + what + ": " + cudaGetErrorString(e);
+  snprintf(g_error, sizeof(g_error), "CUDA error in %s: %s", what, cudaGetErrorString(e));
   if (e == cudaErrorMemoryAllocation) return BSP_ERR_OOM;
   return BSP_ERR_CUDA;
 }
@@ -505,14 +519,14 @@ void stage_work(const bsp_plan* p, double* bytes, double* flops) {
 
 extern "C" {
 
-const char* bsp_last_error(void) { return g_error.c_str(); }
+const char* bsp_last_error(void) { return g_error; }
 
 const char* bsp_version(void) { return "bispec-gb300 0.1 (sm_103a)"; }
 
 bsp_status bsp_plan_create(const bsp_plan_desc* desc, void* stream, bsp_plan** out) {
   if (!out) return fail(BSP_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
-  g_error.clear();
+  g_error[0] = 0;
   bsp_status st = validate(desc);
   if (st != BSP_OK) return st;
   bsp_plan* p = new (std::nothrow) bsp_plan();
