@@ -162,6 +162,30 @@ BSP_API bsp_status bsp_timing_read(bsp_plan* plan, double* ms, int* n_calls, lon
  * flops[s] of its arithmetic core (0 where it is negligible). Host-side, no GPU work. */
 BSP_API bsp_status bsp_plan_stage_work(const bsp_plan* plan, double* bytes, double* flops);
 
+/* Limits of bsp_triple_sums_noalloc (its scratch array has a fixed size). */
+#define BSP_NOALLOC_MAX_TRIPLETS 4096
+#define BSP_NOALLOC_MAX_SHELLS 64
+#define BSP_NOALLOC_MAX_BLOCKS 304
+
+/* Triple-product sums that allocate nothing: msum[t] = sum_x d_a(x) d_b(x) d_c(x) for the bins
+ * triplets[3t..3t+2] = (a, b, c), from FP32 fields[n][v] (n < n_shells, v < n_vox), the layout
+ * bsp_shell_fields writes. The paper has no counterpart of this entry point; it serves callers
+ * that cannot call cudaMalloc: code inside a framework whose allocator owns the whole device
+ * memory budget (a raw cudaMalloc there escapes its accounting), or a loop that must never enter
+ * the driver's allocator after set-up. It needs no plan. Its per-block partial sums live in one
+ * static device array of BSP_NOALLOC_MAX_BLOCKS * BSP_NOALLOC_MAX_TRIPLETS doubles (9.5 MiB) that
+ * every GPU loading this library keeps until the process exits; the first call on a device looks
+ * up that array's address (make this first call before any stream capture). Each call writes
+ * every scratch entry it later reads, so nothing needs clearing, but all calls share the array:
+ * calls that overlap on the GPU (other streams, other threads) race and give wrong sums.
+ * fields, triplets (int, 3 per bin), msum (n_triplets doubles): device pointers, caller-owned.
+ * Errors: BSP_ERR_INVALID_ARG for NULL pointers, n_shells outside [1, BSP_NOALLOC_MAX_SHELLS],
+ * n_triplets outside [1, BSP_NOALLOC_MAX_TRIPLETS] or n_vox < 1; BSP_ERR_CUDA. Shell indices must
+ * be < n_shells (not checked). Accumulates in FP32 over runs of 1024 voxels and in FP64 across. */
+BSP_API bsp_status bsp_triple_sums_noalloc(const float* fields, int n_shells, long long n_vox,
+                                           const int* triplets, int n_triplets, double* msum,
+                                           void* stream);
+
 /* Message of the last failing call on this thread ("" if none). */
 BSP_API const char* bsp_last_error(void);
 

@@ -53,6 +53,8 @@ SIGNATURES = {
     "bsp_timing_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int),
                                   C.POINTER(C.c_longlong)]),
     "bsp_plan_stage_work": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "bsp_triple_sums_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_longlong, C.c_void_p, C.c_int,
+                                          C.c_void_p, C.c_void_p]),
     "bsp_last_error": (C.c_char_p, []),
     "bsp_version": (C.c_char_p, []),
 }
