@@ -137,6 +137,10 @@ BSP_API bsp_status bsp_estimate_host(bsp_plan* plan, const void* spec_host, doub
  * device pointer owned by the plan (n_triplets doubles, valid until the next call on it). */
 BSP_API bsp_status bsp_last_sums(const bsp_plan* plan, const double** msum);
 
+/* Synchronise `stream` and report a device-side failure raised by an earlier call on this plan:
+ * BSP_ERR_TIMEOUT if a bounded wait inside a kernel gave up (the call's results are invalid). */
+BSP_API bsp_status bsp_plan_check(bsp_plan* plan, void* stream);
+
 /* Stages of one bsp_estimate, in launch order (for bsp_timing_read and bsp_plan_stage_work). */
 enum {
   BSP_STAGE_XPASS = 0,    /* shell-masked C2C along x (Eq. (2.8)) */

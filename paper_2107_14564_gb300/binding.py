@@ -87,6 +87,10 @@ def bsp_last_sums(handle) -> int:
     return p.value
 
 
+def bsp_plan_check(handle, stream=None) -> None:
+    check(_lib.load().bsp_plan_check(handle, C.c_void_p(_stream_ptr(stream))))
+
+
 def bsp_version() -> str:
     return _lib.load().bsp_version().decode()
 
@@ -159,6 +163,10 @@ class Plan:
         bsp_estimate_host(self.handle, spec_host, b, g, stream)
         return b, g
 
+    def check(self, stream=None):
+        """Raise if a bounded device-side wait gave up in an earlier call (synchronises)."""
+        bsp_plan_check(self.handle, stream)
+
     def shell_fields(self, spec: torch.Tensor, stream=None) -> torch.Tensor:
         self._check_spec(spec)
         out = torch.empty((self.n_shells, self.ng, self.ng, self.ng), dtype=self.real_dtype,
@@ -177,4 +185,4 @@ class Plan:
 
 __all__ = ["Plan", "BispecError", "bsp_plan_create", "bsp_plan_destroy", "bsp_plan_info",
            "bsp_plan_triplets", "bsp_shell_fields", "bsp_contract", "bsp_estimate",
-           "bsp_estimate_host", "bsp_last_sums", "bsp_version", "TRIPLET_DTYPE"]
+           "bsp_estimate_host", "bsp_last_sums", "bsp_plan_check", "bsp_version", "TRIPLET_DTYPE"]

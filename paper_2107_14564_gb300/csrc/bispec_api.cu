@@ -103,6 +103,13 @@ struct bsp_plan {
   double* tsum = nullptr;
   int* cell_ptr = nullptr;
   int* cell_idx = nullptr;
+  // tensor-core contraction (BSP_MIXED_BF16X3)
+  int tc_np = 0, tc_mtiles = 0, tc_gridy = 0;
+  long long tc_vpb = 0;
+  int2* d_tc_pairs = nullptr;
+  int* d_tc_map = nullptr;
+  double* tc_partial = nullptr;
+  int* d_error = nullptr;
   // per-stage timing (bsp_timing_enable)
   bool timing_on = false;
   int timing_max = 0;
@@ -273,6 +280,8 @@ bsp_status validate(const bsp_plan_desc* d) {
   if (d->precision < BSP_FP64 || d->precision > BSP_MIXED_BF16X3)
     return fail(BSP_ERR_INVALID_ARG, "unknown precision");
   if (d->rsd != 0 && d->rsd != 1) return fail(BSP_ERR_INVALID_ARG, "rsd must be 0 or 1");
+  if (d->precision == BSP_MIXED_BF16X3 && (d->ng % 4 != 0 || d->n_shells > 64))
+    return fail(BSP_ERR_NOT_SUPPORTED, "BSP_MIXED_BF16X3 needs ng % 4 == 0 and at most 64 shells");
   if (d->rsd && !isfinite(d->beta)) return fail(BSP_ERR_INVALID_ARG, "beta must be finite");
   return BSP_OK;
 }
@@ -415,6 +424,46 @@ bsp_status count_triangles(bsp_plan* p, const std::vector<int>& ca, const std::v
   return BSP_OK;
 }
 
+// The contraction of a plan (CUDA cores or tensor cores) and its cross-block sums into msum.
+// `mid` (optional) is recorded between the two launches.
+template <typename T>
+bsp_status run_contract(bsp_plan* p, const void* fields, double* msum, cudaStream_t s, cudaEvent_t mid) {
+  bsp_status st;
+  if (p->prec == BSP_MIXED_BF16X3) {
+    TcArgs a{};
+    a.fields = static_cast<const float*>(fields);
+    a.nvox = p->nvox();
+    a.ns = p->ns;
+    a.np = p->tc_np;
+    a.pair_ab = p->d_tc_pairs;
+    a.n_mtiles = p->tc_mtiles;
+    a.gridy = p->tc_gridy;
+    a.vox_per_block = p->tc_vpb;
+    a.partial = p->tc_partial;
+    a.error = p->d_error;
+    st = launch_contract_tc(a, s);
+    if (st != BSP_OK) return st;
+    if (mid) BSP_CUDA(cudaEventRecord(mid, s));
+    return launch_reduce_tc(a, p->d_tc_map, (int)p->trips.size(), msum, s);
+  }
+  ContractArgs c{};
+  c.fields = fields;
+  c.nvox = p->nvox();
+  c.ns = p->ns;
+  c.tiles = p->d_tiles;
+  c.pairs = p->d_pairs;
+  c.tile_map = p->d_map;
+  c.ntiles = p->ntiles;
+  c.gridx = p->gridx;
+  c.partial = p->partial;
+  c.msum = msum;
+  c.n_out = (int)p->trips.size();
+  st = launch_contract_simt<T>(c, s);
+  if (st != BSP_OK) return st;
+  if (mid) BSP_CUDA(cudaEventRecord(mid, s));
+  return launch_reduce_partials(c, s);
+}
+
 template <typename T>
 bsp_status estimate_impl(bsp_plan* p, const void* spec, double* b_trip, double* b_grid, cudaStream_t s) {
   const bool rec = p->timing_on && p->timing_calls < p->timing_max;
@@ -444,22 +493,7 @@ bsp_status estimate_impl(bsp_plan* p, const void* spec, double* b_trip, double* 
   st = launch_zpass<T>(a, p->nzi, p->lines_z, s);
   if (st != BSP_OK) return st;
   if (rec) BSP_CUDA(cudaEventRecord(ev[3], s));
-  ContractArgs c{};
-  c.fields = p->fields;
-  c.nvox = p->nvox();
-  c.ns = p->ns;
-  c.tiles = p->d_tiles;
-  c.pairs = p->d_pairs;
-  c.tile_map = p->d_map;
-  c.ntiles = p->ntiles;
-  c.gridx = p->gridx;
-  c.partial = p->partial;
-  c.msum = p->msum;
-  c.n_out = (int)p->trips.size();
-  st = launch_contract_simt<T>(c, s);
-  if (st != BSP_OK) return st;
-  if (rec) BSP_CUDA(cudaEventRecord(ev[4], s));
-  st = launch_reduce_partials(c, s);
+  st = run_contract<T>(p, p->fields, p->msum, s, rec ? ev[4] : nullptr);
   if (st != BSP_OK) return st;
   FinalizeArgs f{};
   f.msum = p->msum;
@@ -477,7 +511,8 @@ bsp_status estimate_impl(bsp_plan* p, const void* spec, double* b_trip, double* 
   if (rec) {
     BSP_CUDA(cudaEventRecord(ev[5], s));
     p->timing_calls += 1;
-    p->launches += (p->nxi > 0) + (p->nyi > 0) + (p->nzi > 0) + 2 * (p->ntiles > 0) + 1;
+    const int ncontract = p->prec == BSP_MIXED_BF16X3 ? 2 * (p->tc_mtiles > 0) : 2 * (p->ntiles > 0);
+    p->launches += (p->nxi > 0) + (p->nyi > 0) + (p->nzi > 0) + ncontract + 1;
   }
   return BSP_OK;
 }
@@ -626,6 +661,35 @@ bsp_status bsp_plan_create(const bsp_plan_desc* desc, void* stream, bsp_plan** o
   TRY(dev_alloc(p, std::max<size_t>(p->trips.size(), 1) * sizeof(double), &tmp));
   p->msum = static_cast<double*>(tmp);
   TRY(dev_upload(p, kt, &p->tsum, s));
+  {
+    std::vector<int> zero(1, 0);
+    TRY(dev_upload(p, zero, &p->d_error, s));
+  }
+  if (p->prec == BSP_MIXED_BF16X3) {
+    p->tc_np = tc_padded_shells(p->ns);
+    const int np = (int)pairs.size();
+    p->tc_mtiles = (np + 127) / 128;
+    std::vector<int2> pab((size_t)std::max(p->tc_mtiles, 1) * 128, make_int2(-1, -1));
+    for (int i = 0; i < np; ++i) pab[i] = pairs[i];
+    // map of every kept bin to its (pair row, c) entry
+    std::vector<int> tmap(p->trips.size());
+    {
+      int pi = -1;
+      for (size_t t = 0; t < p->trips.size(); ++t) {
+        if (t == 0 || p->trips[t].a != p->trips[t - 1].a || p->trips[t].b != p->trips[t - 1].b) ++pi;
+        tmap[t] = pi * p->tc_np + p->trips[t].c;
+      }
+    }
+    const long long chunks = p->nvox() / 64;
+    long long gy = std::max<long long>(1, (2LL * p->n_sm) / std::max(p->tc_mtiles, 1));
+    gy = std::min(gy, chunks);
+    p->tc_vpb = ((chunks + gy - 1) / gy) * 64;
+    p->tc_gridy = (int)((p->nvox() + p->tc_vpb - 1) / p->tc_vpb);
+    TRY(dev_upload(p, pab, &p->d_tc_pairs, s));
+    TRY(dev_upload(p, tmap, &p->d_tc_map, s));
+    TRY(dev_alloc(p, tc_partial_doubles(std::max(p->tc_mtiles, 1), p->tc_gridy, p->tc_np) * sizeof(double), &tmp));
+    p->tc_partial = static_cast<double*>(tmp);
+  }
   TRY(dev_upload(p, cptr, &p->cell_ptr, s));
   TRY(dev_upload(p, cidx, &p->cell_idx, s));
   e = cudaStreamSynchronize(s);
@@ -675,22 +739,19 @@ bsp_status bsp_shell_fields(bsp_plan* p, const void* spec, void* fields_out, voi
 
 bsp_status bsp_contract(bsp_plan* p, const void* fields, double* msum, void* stream) {
   if (!p || !fields || !msum) return fail(BSP_ERR_INVALID_ARG, "NULL argument");
+  if ((reinterpret_cast<uintptr_t>(fields) & 15) != 0) return fail(BSP_ERR_INVALID_ARG, "fields must be 16-byte aligned");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  ContractArgs c{};
-  c.fields = fields;
-  c.nvox = p->nvox();
-  c.ns = p->ns;
-  c.tiles = p->d_tiles;
-  c.pairs = p->d_pairs;
-  c.tile_map = p->d_map;
-  c.ntiles = p->ntiles;
-  c.gridx = p->gridx;
-  c.partial = p->partial;
-  c.msum = msum;
-  c.n_out = (int)p->trips.size();
-  bsp_status st = p->prec == BSP_FP64 ? launch_contract_simt<double>(c, s) : launch_contract_simt<float>(c, s);
-  if (st != BSP_OK) return st;
-  return launch_reduce_partials(c, s);
+  if (p->prec == BSP_FP64) return run_contract<double>(p, fields, msum, s, nullptr);
+  return run_contract<float>(p, fields, msum, s, nullptr);
+}
+
+bsp_status bsp_plan_check(bsp_plan* p, void* stream) {
+  if (!p) return fail(BSP_ERR_INVALID_ARG, "plan is NULL");
+  BSP_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+  int flag = 0;
+  BSP_CUDA(cudaMemcpy(&flag, p->d_error, sizeof(int), cudaMemcpyDeviceToHost));
+  if (flag) return fail(BSP_ERR_TIMEOUT, "a bounded device-side wait gave up in an earlier call");
+  return BSP_OK;
 }
 
 bsp_status bsp_estimate(bsp_plan* p, const void* spec, double* b_triplet, double* b_grid, void* stream) {

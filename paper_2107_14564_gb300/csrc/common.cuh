@@ -130,4 +130,23 @@ struct FinalizeArgs {
 };
 bsp_status launch_finalize(const FinalizeArgs& a, cudaStream_t s);
 
+// ---------------------------------------------------------------- tensor-core contraction
+struct TcArgs {
+  const float* fields;      // [ns][nvox] FP32, 16-byte aligned
+  long long nvox;           // multiple of 64
+  int ns;
+  int np;                   // shells padded for the MMA N dimension (32 or 64)
+  const int2* pair_ab;      // [n_mtiles * 128] (a, b), (-1, -1) on padding rows
+  int n_mtiles;
+  int gridy;                // voxel blocks
+  long long vox_per_block;  // multiple of 64
+  double* partial;          // [gridy][n_mtiles][128][np]
+  int* error;               // set to 1 when a bounded wait gives up
+};
+int tc_padded_shells(int ns);
+size_t tc_partial_doubles(int n_mtiles, int gridy, int np);
+bsp_status launch_contract_tc(const TcArgs& a, cudaStream_t s);
+// msum[t] = sum_y partial[y][map[t]], map[t] = (mtile * 128 + row) * np + c of bin t
+bsp_status launch_reduce_tc(const TcArgs& a, const int* map, int n_out, double* msum, cudaStream_t s);
+
 }  // namespace bsp

@@ -130,7 +130,7 @@ def _cond_err(b, res):
     return np.abs(b - res["b"]) / res["b_scale"]
 
 
-@pytest.mark.parametrize("prec", ["fp32"])
+@pytest.mark.parametrize("prec", ["fp32", "mixed_bf16x3"])
 def test_fp32_parity_ragged(lib, prec):
     """Ng=64 with 12 shells: several contraction tiles and voxel chunks; FP32 within 1e-4 of the
     condition scale (the relative error itself is reported by the bench)."""
@@ -179,3 +179,32 @@ def test_errors_are_reported(lib):
     assert e.value.status == 6
     with pytest.raises(lib.BispecError):
         lib.Plan(32, 32.0, [1.5, 1.6])               # empty shell
+
+
+@pytest.mark.parametrize("ng,ns,top", [(32, 6, 8.0), (64, 12, 16.0), (128, 40, 32.0)])
+def test_mixed_contraction_shapes(lib, ng, ns, top):
+    """Tensor-core contraction with 6 (padded to 32), 12 and 40 (padded to 64) shells; bins
+    spread over one to several M tiles of 128 pairs. Within 1e-4 of the condition scale."""
+    edges = P.linear_edges(ns, 1.0, top)
+    spec = _spec(ng, 1.5, 0.1, 30 + ns, c64=True)
+    pl, res = _oracle(spec, ng, edges, with_abs=True)
+    gp = lib.Plan(ng, float(ng), edges, precision="mixed_bf16x3")
+    b, _ = gp.estimate(torch.from_numpy(spec).cuda())
+    gp.check()
+    err = _cond_err(b.cpu().numpy(), res)
+    assert np.max(err) < 1e-4, np.max(err)
+
+
+def test_mixed_contract_on_oracle_fields(lib):
+    """The tensor-core contraction alone, fed FP32 copies of the oracle's fields."""
+    ng = 64
+    edges = _edges(ng, 10)
+    spec = _spec(ng, 2.0, 0.1, 8, c64=False)
+    pl, res = _oracle(spec, ng, edges, with_abs=True)
+    fields = fbe.shell_fields(spec, pl)
+    stack = np.stack([fields[n] for n in range(pl.ns)]).astype(np.float32)
+    exact = fbe.triple_sums({n: stack[n].astype(np.float64) for n in range(pl.ns)}, res["triplets"])
+    gp = lib.Plan(ng, float(ng), edges, precision="mixed_bf16x3")
+    msum = gp.contract(torch.from_numpy(stack).cuda()).cpu().numpy()
+    gp.check()
+    assert np.max(np.abs(msum - exact) / res["asum"]) < 1e-4
