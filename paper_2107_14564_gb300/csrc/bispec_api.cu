@@ -280,8 +280,8 @@ bsp_status validate(const bsp_plan_desc* d) {
   if (d->precision < BSP_FP64 || d->precision > BSP_MIXED_BF16X3)
     return fail(BSP_ERR_INVALID_ARG, "unknown precision");
   if (d->rsd != 0 && d->rsd != 1) return fail(BSP_ERR_INVALID_ARG, "rsd must be 0 or 1");
-  if (d->precision == BSP_MIXED_BF16X3 && (d->ng % 4 != 0 || d->n_shells > 64))
-    return fail(BSP_ERR_NOT_SUPPORTED, "BSP_MIXED_BF16X3 needs ng % 4 == 0 and at most 64 shells");
+  if (d->precision == BSP_MIXED_BF16X3 && (d->ng % 8 != 0 || d->n_shells > 64))
+    return fail(BSP_ERR_NOT_SUPPORTED, "BSP_MIXED_BF16X3 needs ng % 8 == 0 and at most 64 shells");
   if (d->rsd && !isfinite(d->beta)) return fail(BSP_ERR_INVALID_ARG, "beta must be finite");
   return BSP_OK;
 }
@@ -680,10 +680,11 @@ bsp_status bsp_plan_create(const bsp_plan_desc* desc, void* stream, bsp_plan** o
         tmap[t] = pi * p->tc_np + p->trips[t].c;
       }
     }
-    const long long chunks = p->nvox() / 64;
-    long long gy = std::max<long long>(1, (2LL * p->n_sm) / std::max(p->tc_mtiles, 1));
+    const long long chunks = p->nvox() / kTcVoxelChunk;
+    // one block per SM and voxel range; the M tiles of one range run side by side (L2 reuse)
+    long long gy = std::max(1, p->n_sm);
     gy = std::min(gy, chunks);
-    p->tc_vpb = ((chunks + gy - 1) / gy) * 64;
+    p->tc_vpb = ((chunks + gy - 1) / gy) * kTcVoxelChunk;
     p->tc_gridy = (int)((p->nvox() + p->tc_vpb - 1) / p->tc_vpb);
     TRY(dev_upload(p, pab, &p->d_tc_pairs, s));
     TRY(dev_upload(p, tmap, &p->d_tc_map, s));

@@ -131,15 +131,16 @@ struct FinalizeArgs {
 bsp_status launch_finalize(const FinalizeArgs& a, cudaStream_t s);
 
 // ---------------------------------------------------------------- tensor-core contraction
+constexpr int kTcVoxelChunk = 128;  // voxels per pipeline stage of the tensor-core contraction
 struct TcArgs {
   const float* fields;      // [ns][nvox] FP32, 16-byte aligned
-  long long nvox;           // multiple of 64
+  long long nvox;           // multiple of kTcVoxelChunk
   int ns;
   int np;                   // shells padded for the MMA N dimension (32 or 64)
   const int2* pair_ab;      // [n_mtiles * 128] (a, b), (-1, -1) on padding rows
   int n_mtiles;
   int gridy;                // voxel blocks
-  long long vox_per_block;  // multiple of 64
+  long long vox_per_block;  // multiple of kTcVoxelChunk
   double* partial;          // [gridy][n_mtiles][128][np]
   int* error;               // set to 1 when a bounded wait gives up
 };

@@ -47,6 +47,24 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
+// ------------------------------------------------------------------ bulk copies (TMA, 1D)
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// global -> shared copy of `bytes` (multiple of 16, both addresses 16-byte aligned), completing
+// `bytes` transactions on the mbarrier.
+__device__ __forceinline__ void bulk_g2s(void* smem_dst, const void* gmem_src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(smem_dst)),
+      "l"(gmem_src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
 // ------------------------------------------------------------------ proxy fences
 // Make generic-proxy shared-memory writes visible to the async proxy (the tensor core).
 __device__ __forceinline__ void fence_proxy_async_smem() {
@@ -81,6 +99,11 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* v) {
       "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
       : "memory");
 }
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t* v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+               "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+               : "memory");
+}
 __device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* v) {
@@ -91,6 +114,12 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* v) {
         "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
       : "r"(taddr)
       : "memory");
+}
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* v) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+               : "r"(taddr)
+               : "memory");
 }
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
@@ -139,6 +168,59 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
 }
 __device__ __forceinline__ float bf16lo_to_f32(uint32_t v) { return __uint_as_float(v << 16); }
 __device__ __forceinline__ float bf16hi_to_f32(uint32_t v) { return __uint_as_float(v & 0xFFFF0000u); }
+
+// ------------------------------------------------------------------ packed FP32 pairs
+__device__ __forceinline__ uint64_t f2_pack(float lo, float hi) {
+  return (uint64_t)__float_as_uint(lo) | ((uint64_t)__float_as_uint(hi) << 32);
+}
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+// Split a packed pair x = (x0, x1) into bf16 high parts (round to nearest) and the bf16 rounding
+// of the remainders x - high: returns (hi pair, lo pair) as two packed bf16x2 words.
+__device__ __forceinline__ void split_bf16x2(uint64_t x, uint32_t& hi, uint32_t& lo) {
+  const float x0 = __uint_as_float((uint32_t)x);
+  const float x1 = __uint_as_float((uint32_t)(x >> 32));
+  hi = pack_bf16x2(x0, x1);
+  const uint64_t h = (uint64_t)(hi << 16) | ((uint64_t)(hi & 0xFFFF0000u) << 32);
+  const uint64_t r = f2_sub(x, h);
+  lo = pack_bf16x2(__uint_as_float((uint32_t)r), __uint_as_float((uint32_t)(r >> 32)));
+}
+
+// Pair product of two bf16-split values, a = ah + al and b = bh + bl (two lanes per word):
+// ph = bf16(ah bh); the exact rounding error e = ah bh - ph (an FMA, exact in bf16 because the
+// product of two 8-bit significands has at most 16 bits); pl = bf16(ah bl + bf16(al bh + e)).
+// ph + pl equals a b to about 2^-16 relative (al bl, below 2^-18, is dropped).
+__device__ __forceinline__ void bf16x2_pair_product(uint32_t ah, uint32_t al, uint32_t bh, uint32_t bl,
+                                                    uint32_t& ph, uint32_t& pl) {
+  uint32_t nph, e, t;
+  asm("mul.rn.bf16x2 %0, %1, %2;" : "=r"(ph) : "r"(ah), "r"(bh));
+  asm("neg.bf16x2 %0, %1;" : "=r"(nph) : "r"(ph));
+  asm("fma.rn.bf16x2 %0, %1, %2, %3;" : "=r"(e) : "r"(ah), "r"(bh), "r"(nph));
+  asm("fma.rn.bf16x2 %0, %1, %2, %3;" : "=r"(t) : "r"(al), "r"(bh), "r"(e));
+  asm("fma.rn.bf16x2 %0, %1, %2, %3;" : "=r"(pl) : "r"(ah), "r"(bl), "r"(t));
+}
+
+// Barrier over `nthreads` threads (a multiple of 32) that also ORs a flag across them.
+__device__ __forceinline__ bool named_barrier_or(int id, int nthreads, bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 q, %1, 0;\n\t"
+      "bar.red.or.pred p, %2, %3, q;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v), "r"(id), "r"(nthreads)
+      : "memory");
+  return r != 0;
+}
 
 }  // namespace ptx
 }  // namespace bsp
