@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <string>
 #include <vector>
 
@@ -103,6 +104,11 @@ struct bsp_plan {
   double* tsum = nullptr;
   int* cell_ptr = nullptr;
   int* cell_idx = nullptr;
+  // warp-per-line FP32 passes
+  bool warp_fft = false;
+  Item *d_wxi = nullptr, *d_wyi = nullptr;
+  int nwxi = 0, nwyi = 0;
+  int rmax = 0;
   // tensor-core contraction (BSP_MIXED_BF16X3)
   int tc_np = 0, tc_mtiles = 0, tc_gridy = 0;
   long long tc_vpb = 0;
@@ -464,35 +470,60 @@ bsp_status run_contract(bsp_plan* p, const void* fields, double* msum, cudaStrea
   return launch_reduce_partials(c, s);
 }
 
+// The three pass launches of an estimate on the plan's buffers; ev (optional) receives an event
+// after the X and after the Y pass, and after the Z pass.
 template <typename T>
-bsp_status estimate_impl(bsp_plan* p, const void* spec, double* b_trip, double* b_grid, cudaStream_t s) {
-  const bool rec = p->timing_on && p->timing_calls < p->timing_max;
-  cudaEvent_t* ev = rec ? &p->events[(size_t)p->timing_calls * (BSP_N_STAGES + 1)] : nullptr;
-  if (rec) BSP_CUDA(cudaEventRecord(ev[0], s));
+bsp_status plan_passes(bsp_plan* p, const void* spec, void* fields, cudaStream_t s, cudaEvent_t* ev) {
   PassArgs a{};
   a.spec = spec;
   a.g1 = p->g1;
   a.g2 = p->g2;
-  a.fields = p->fields;
+  a.fields = fields;
   a.tw = p->tw;
   a.geom = p->d_geom;
   a.ng = p->ng;
   a.rsd = p->rsd;
   a.beta = p->beta;
+  a.rmax = p->rmax;
+  bsp_status st;
+  if (std::is_same<T, float>::value && p->warp_fft) {
+    a.items = p->d_wxi;
+    st = launch_warp_xpass(a, p->nwxi, s);
+    if (st != BSP_OK) return st;
+    if (ev) BSP_CUDA(cudaEventRecord(ev[0], s));
+    a.items = p->d_wyi;
+    st = launch_warp_ypass(a, p->nwyi, s);
+    if (st != BSP_OK) return st;
+    if (ev) BSP_CUDA(cudaEventRecord(ev[1], s));
+    st = launch_warp_zpass(a, (long long)p->ns * p->ng * p->ng, p->n_sm, s);
+    if (st != BSP_OK) return st;
+    if (ev) BSP_CUDA(cudaEventRecord(ev[2], s));
+    return BSP_OK;
+  }
   a.st = p->st_full;
   a.items = p->d_xi;
-  bsp_status st = launch_xpass<T>(a, p->nxi, p->lines_xy, s);
+  st = launch_xpass<T>(a, p->nxi, p->lines_xy, s);
   if (st != BSP_OK) return st;
-  if (rec) BSP_CUDA(cudaEventRecord(ev[1], s));
+  if (ev) BSP_CUDA(cudaEventRecord(ev[0], s));
   a.items = p->d_yi;
   st = launch_ypass<T>(a, p->nyi, p->lines_xy, s);
   if (st != BSP_OK) return st;
-  if (rec) BSP_CUDA(cudaEventRecord(ev[2], s));
+  if (ev) BSP_CUDA(cudaEventRecord(ev[1], s));
   a.items = p->d_zi;
   a.st = p->st_half;
   st = launch_zpass<T>(a, p->nzi, p->lines_z, s);
   if (st != BSP_OK) return st;
-  if (rec) BSP_CUDA(cudaEventRecord(ev[3], s));
+  if (ev) BSP_CUDA(cudaEventRecord(ev[2], s));
+  return BSP_OK;
+}
+
+template <typename T>
+bsp_status estimate_impl(bsp_plan* p, const void* spec, double* b_trip, double* b_grid, cudaStream_t s) {
+  const bool rec = p->timing_on && p->timing_calls < p->timing_max;
+  cudaEvent_t* ev = rec ? &p->events[(size_t)p->timing_calls * (BSP_N_STAGES + 1)] : nullptr;
+  if (rec) BSP_CUDA(cudaEventRecord(ev[0], s));
+  bsp_status st = plan_passes<T>(p, spec, p->fields, s, rec ? ev + 1 : nullptr);
+  if (st != BSP_OK) return st;
   st = run_contract<T>(p, p->fields, p->msum, s, rec ? ev[4] : nullptr);
   if (st != BSP_OK) return st;
   FinalizeArgs f{};
@@ -649,6 +680,16 @@ bsp_status bsp_plan_create(const bsp_plan_desc* desc, void* stream, bsp_plan** o
   TRY(dev_upload(p, xi, &p->d_xi, s));
   TRY(dev_upload(p, yi, &p->d_yi, s));
   TRY(dev_upload(p, zi, &p->d_zi, s));
+  for (const ShellGeom& g : p->geom) p->rmax = std::max(p->rmax, g.r);
+  p->warp_fft = p->prec != BSP_FP64 && warp_fft_supported(p->ng);
+  if (p->warp_fft) {
+    std::vector<Item> wx, wy, wz;
+    make_items(p, warp_fft_lines(), 1, wx, wy, wz);
+    p->nwxi = (int)wx.size();
+    p->nwyi = (int)wy.size();
+    TRY(dev_upload(p, wx, &p->d_wxi, s));
+    TRY(dev_upload(p, wy, &p->d_wyi, s));
+  }
   TRY(dev_alloc(p, g1_elems(p) * ce, &p->g1));
   TRY(dev_alloc(p, g2_elems(p) * ce, &p->g2));
   TRY(dev_alloc(p, p->field_bytes(), &p->fields));
@@ -731,11 +772,8 @@ bsp_status bsp_plan_triplets(const bsp_plan* p, const bsp_triplet** table, int* 
 bsp_status bsp_shell_fields(bsp_plan* p, const void* spec, void* fields_out, void* stream) {
   if (!p || !spec || !fields_out) return fail(BSP_ERR_INVALID_ARG, "NULL argument");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (p->prec == BSP_FP64)
-    return run_passes<double>(p, spec, p->rsd, p->tw, p->g1, p->g2, fields_out, p->d_xi, p->nxi, p->d_yi,
-                              p->nyi, p->d_zi, p->nzi, p->lines_xy, p->lines_z, s);
-  return run_passes<float>(p, spec, p->rsd, p->tw, p->g1, p->g2, fields_out, p->d_xi, p->nxi, p->d_yi,
-                           p->nyi, p->d_zi, p->nzi, p->lines_xy, p->lines_z, s);
+  if (p->prec == BSP_FP64) return plan_passes<double>(p, spec, fields_out, s, nullptr);
+  return plan_passes<float>(p, spec, fields_out, s, nullptr);
 }
 
 bsp_status bsp_contract(bsp_plan* p, const void* fields, double* msum, void* stream) {

@@ -70,7 +70,16 @@ struct PassArgs {
   int rsd;
   double beta;
   FftStages st;           // stage list of this pass's line length
+  int rmax;               // largest r of all shells
 };
+
+// Warp-per-line FP32 passes (bispec_fft_warp.cu) for power-of-two grids 128..1024; X/Y items
+// hold at most warp_fft_lines() lines.
+bool warp_fft_supported(int ng);
+int warp_fft_lines();
+bsp_status launch_warp_xpass(const PassArgs& a, int n_items, cudaStream_t s);
+bsp_status launch_warp_ypass(const PassArgs& a, int n_items, cudaStream_t s);
+bsp_status launch_warp_zpass(const PassArgs& a, long long n_lines, int n_sm, cudaStream_t s);
 
 // ---------------------------------------------------------------- contraction tables
 // A tile covers up to 4 consecutive pairs and 4 consecutive c shells; map[16] gives the kept
