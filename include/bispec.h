@@ -106,17 +106,27 @@ BSP_API bsp_status bsp_plan_destroy(bsp_plan* plan);
 BSP_API bsp_status bsp_plan_info(const bsp_plan* plan, int* n_triplets, int* n_shells,
                          size_t* field_bytes, size_t* device_bytes);
 
+/* Side of the plan's evaluation grid, ng_eval <= ng. Every shell mode has |m_i| <= r - 1, so a
+ * triple product of shell fields only holds wavevectors with |k_i| <= 3 (r - 1); summed over any
+ * grid of side S > 3 (r - 1) it keeps only k = 0, exactly as the ng^3 grid of Eq. (2.7) does (the
+ * plane-wave identity of Eq. (2.6) and the cap after Eq. (2.12)). The plan samples the shell
+ * fields (Eq. (2.8), (2.11)) on the smallest such S it has kernels for and scales its sums by
+ * (ng / S)^3; results are those of the ng^3 grid up to rounding. */
+BSP_API bsp_status bsp_plan_grid(const bsp_plan* plan, int* ng_eval);
+
 /* The kept bins, in ascending (a, b, c) order; the host table is owned by the plan. */
 BSP_API bsp_status bsp_plan_triplets(const bsp_plan* plan, const bsp_triplet** table, int* n);
 
-/* Shell fields, Eq. (2.8): fields_out[n][x][y][z] = d_n(x) for n < N_s (device, caller-owned,
- * N_s * Ng^3 reals: double for BSP_FP64 plans, float otherwise). With rsd=1 the Kaiser factor
- * of Eq. (3.4) is applied to the spectrum first. spec: device half spectrum (see top). */
+/* Shell fields, Eq. (2.8), sampled on the plan's evaluation grid (S = bsp_plan_grid):
+ * fields_out[n][i][j][l] = d_n(x) at x = (i, j, l) L / S for n < N_s (device, caller-owned,
+ * N_s * S^3 reals: double for BSP_FP64 plans, float otherwise). With rsd=1 the Kaiser factor of
+ * Eq. (3.4) is applied to the spectrum first. spec: device half spectrum of the ng grid. */
 BSP_API bsp_status bsp_shell_fields(bsp_plan* plan, const void* spec, void* fields_out, void* stream);
 
-/* Triple-product sums, the numerator of Eq. (2.7): msum[t] = sum_x d_a d_b d_c for every kept
- * bin t, from shell fields laid out as bsp_shell_fields writes them (device, read-only).
- * msum: device, n_triplets doubles. Uses the plan's contraction (bsp_precision). */
+/* Triple-product sums, the numerator of Eq. (2.7): msum[t] = sum_x d_a d_b d_c over the ng^3 grid
+ * for every kept bin t, from shell fields on the evaluation grid laid out as bsp_shell_fields
+ * writes them (device, read-only, 16-byte aligned); computed as (ng / S)^3 times the sum over
+ * the S^3 grid. msum: device, n_triplets doubles. Uses the plan's contraction (bsp_precision). */
 BSP_API bsp_status bsp_contract(bsp_plan* plan, const void* fields, double* msum, void* stream);
 
 /* The whole estimator on one field, Eqs. (2.7)-(2.11) and the (mu, t) map:

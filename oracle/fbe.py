@@ -48,6 +48,24 @@ def shell_fields(spec_half: np.ndarray, plan: P.Plan, shells=None, workers: int 
     return out
 
 
+def shell_fields_on_grid(spec_half: np.ndarray, plan: P.Plan, size: int, shells=None, workers: int = -1):
+    """d_n of Eq. (2.8) sampled at x = (i, j, l) L / size on a size^3 grid, for a size that holds
+    every shell mode (|m_i| < size / 2): each shell's modes are copied from the ng half spectrum
+    into a size^3 half spectrum, which is inverse transformed (unnormalised)."""
+    ng = plan.ng
+    sidx = P.shell_index_half(plan)
+    m = np.fft.fftfreq(size, d=1.0 / size).astype(np.int64) % ng
+    mz = np.arange(size // 2 + 1)
+    sub_spec = spec_half[np.ix_(m, m, mz)]
+    sub_idx = sidx[np.ix_(m, m, mz)]
+    shells = range(plan.ns) if shells is None else shells
+    out = {}
+    for n in shells:
+        masked = np.where(sub_idx == n, sub_spec, 0.0).astype(np.complex128)
+        out[n] = sfft.irfftn(masked, s=(size, size, size), workers=workers) * float(size) ** 3
+    return out
+
+
 def counting_fields(plan: P.Plan, shells=None, workers: int = -1):
     """i_n(x) = sum_{k in n} e^{+i k.x} (Eq. (2.11))."""
     ng = plan.ng

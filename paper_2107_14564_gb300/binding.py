@@ -46,6 +46,12 @@ def bsp_plan_info(handle):
     return nt.value, ns.value, fb.value, db.value
 
 
+def bsp_plan_grid(handle) -> int:
+    n = C.c_int()
+    check(_lib.load().bsp_plan_grid(handle, C.byref(n)))
+    return n.value
+
+
 def bsp_plan_triplets(handle) -> np.ndarray:
     tab = C.POINTER(Triplet)()
     n = C.c_int()
@@ -125,6 +131,7 @@ class Plan:
         self.complex_dtype = torch.complex128 if precision == "fp64" else torch.complex64
         self.n_triplets, self.n_shells, self.field_bytes, self.device_bytes = bsp_plan_info(self.handle)
         self.triplets = bsp_plan_triplets(self.handle)
+        self.ng_eval = bsp_plan_grid(self.handle)
 
     def close(self):
         if self.handle is not None:
@@ -169,20 +176,20 @@ class Plan:
 
     def shell_fields(self, spec: torch.Tensor, stream=None) -> torch.Tensor:
         self._check_spec(spec)
-        out = torch.empty((self.n_shells, self.ng, self.ng, self.ng), dtype=self.real_dtype,
-                          device=spec.device)
+        s = self.ng_eval
+        out = torch.empty((self.n_shells, s, s, s), dtype=self.real_dtype, device=spec.device)
         bsp_shell_fields(self.handle, spec, out, stream)
         return out
 
     def contract(self, fields: torch.Tensor, stream=None) -> torch.Tensor:
         if not fields.is_cuda or fields.dtype != self.real_dtype or not fields.is_contiguous() \
-                or fields.numel() != self.n_shells * self.ng ** 3:
-            raise ValueError("fields must be the contiguous [Ns, Ng, Ng, Ng] output of shell_fields")
+                or fields.numel() != self.n_shells * self.ng_eval ** 3:
+            raise ValueError("fields must be the contiguous [Ns, S, S, S] output of shell_fields")
         msum = torch.empty(self.n_triplets, dtype=torch.float64, device=fields.device)
         bsp_contract(self.handle, fields, msum, stream)
         return msum
 
 
 __all__ = ["Plan", "BispecError", "bsp_plan_create", "bsp_plan_destroy", "bsp_plan_info",
-           "bsp_plan_triplets", "bsp_shell_fields", "bsp_contract", "bsp_estimate",
+           "bsp_plan_triplets", "bsp_plan_grid", "bsp_shell_fields", "bsp_contract", "bsp_estimate",
            "bsp_estimate_host", "bsp_last_sums", "bsp_plan_check", "bsp_version", "TRIPLET_DTYPE"]

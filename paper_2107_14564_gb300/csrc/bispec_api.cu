@@ -75,6 +75,8 @@ using namespace bsp;
 struct bsp_plan {
   // description
   int ng = 0, ns = 0, n_mu = 0, n_t = 0, rsd = 0, prec = 0;
+  int ngs = 0;              // side of the evaluation grid (<= ng), see choose_eval_grid
+  double sum_scale = 1.0;   // (ng / ngs)^3: sums over the ng^3 grid from sums over ngs^3
   double box_len = 0.0, beta = 0.0;
   std::vector<double> edges;
   std::vector<long long> q;       // integer thresholds Q_n
@@ -128,7 +130,7 @@ struct bsp_plan {
   double* bgrid_dev = nullptr;
 
   size_t elem() const { return prec == BSP_FP64 ? sizeof(double) : sizeof(float); }
-  long long nvox() const { return (long long)ng * ng * ng; }
+  long long nvox() const { return (long long)ngs * ngs * ngs; }  // voxels of the evaluation grid
   int n_cells() const { return ns * n_mu * n_t; }
   size_t spec_bytes() const { return (size_t)ng * ng * (ng / 2 + 1) * 2 * elem(); }
   size_t field_bytes() const { return (size_t)ns * (size_t)nvox() * elem(); }
@@ -181,7 +183,7 @@ int fft_lines_for(int len, int prec) {
 
 void make_items(const bsp_plan* p, int lines_xy, int lines_z, std::vector<Item>& xi,
                 std::vector<Item>& yi, std::vector<Item>& zi) {
-  const int ng = p->ng;
+  const int ng = p->ngs;
   xi.clear(); yi.clear(); zi.clear();
   for (int n = 0; n < p->ns; ++n) {
     const ShellGeom& g = p->geom[n];
@@ -244,6 +246,7 @@ bsp_status run_passes(const bsp_plan* p, const void* spec, int rsd, void* tw, vo
   a.tw = tw;
   a.geom = p->d_geom;
   a.ng = p->ng;
+  a.ngs = p->ngs;
   a.rsd = rsd;
   a.beta = p->beta;
   a.st = p->st_full;
@@ -290,6 +293,37 @@ bsp_status validate(const bsp_plan_desc* d) {
     return fail(BSP_ERR_NOT_SUPPORTED, "BSP_MIXED_BF16X3 needs ng % 8 == 0 and at most 64 shells");
   if (d->rsd && !isfinite(d->beta)) return fail(BSP_ERR_INVALID_ARG, "beta must be finite");
   return BSP_OK;
+}
+
+// The evaluation grid. Every shell mode has |m_i| <= r_max - 1, so a triple product of three shell
+// fields only holds wavevectors with |k_i| <= 3 (r_max - 1). Summing it over any grid of side
+// S > 3 (r_max - 1) keeps only k = 0, exactly as the ng^3 grid does (the argument of Eq. (2.6) and
+// of the cap after Eq. (2.12)): sum over ng^3 = (ng / S)^3 sum over S^3, and the shell fields
+// sampled on the S grid are the same band-limited functions. The plan evaluates fields and
+// triple products on the smallest such S it has kernels for (at most ng).
+bool fft_size_ok(int n) {
+  if (n < 16 || n % 8 != 0) return false;
+  int m = n;
+  while (m % 2 == 0) m /= 2;
+  while (m % 3 == 0) m /= 3;
+  return m == 1;
+}
+
+void choose_eval_grid(bsp_plan* p) {
+  int rmax = 0;
+  for (int n = 0; n < p->ns; ++n) rmax = std::max(rmax, (int)isqrt_ll(p->q[n + 1] - 1) + 1);
+  const int need = 3 * (rmax - 1) + 1;  // S >= need
+  int best = p->ng;
+  for (int sz = 16; sz < p->ng; ++sz) {
+    if (sz < need || !fft_size_ok(sz)) continue;
+    // FP32 plans prefer the sizes the warp-per-line kernels handle
+    if (p->prec != BSP_FP64 && p->ng >= 128 && !warp_fft_supported(sz)) continue;
+    best = sz;
+    break;
+  }
+  p->ngs = best;
+  const double f = (double)p->ng / (double)p->ngs;
+  p->sum_scale = f * f * f;
 }
 
 // Host part of the plan (Sec. 2.1): thresholds, cap, mode counts, means, geometry.
@@ -342,8 +376,9 @@ bsp_status host_plan(bsp_plan* p, const bsp_plan_desc* d) {
     p->nmodes[n] = c;
     p->kbar[n] = s / (double)c;
   }
-  make_stages(p->ng, &p->st_full);
-  make_stages(p->ng / 2, &p->st_half);
+  choose_eval_grid(p);
+  make_stages(p->ngs, &p->st_full);
+  make_stages(p->ngs / 2, &p->st_half);
   // geometry: complex offsets of each shell in the X and Y pass buffers
   p->geom.resize(p->ns);
   long long o1 = 0, o2 = 0;
@@ -355,26 +390,26 @@ bsp_status host_plan(bsp_plan* p, const bsp_plan_desc* d) {
     g.pad = 0;
     g.g1_off = o1;
     g.g2_off = o2;
-    o1 += (long long)p->ng * (2 * g.r - 1) * g.r;
-    o2 += (long long)p->ng * p->ng * g.r;
+    o1 += (long long)p->ngs * (2 * g.r - 1) * g.r;
+    o2 += (long long)p->ngs * p->ngs * g.r;
   }
   return BSP_OK;
 }
 
 long long g1_elems(const bsp_plan* p) {
   const ShellGeom& g = p->geom.back();
-  return g.g1_off + (long long)p->ng * (2 * g.r - 1) * g.r;
+  return g.g1_off + (long long)p->ngs * (2 * g.r - 1) * g.r;
 }
 long long g2_elems(const bsp_plan* p) {
   const ShellGeom& g = p->geom.back();
-  return g.g2_off + (long long)p->ng * p->ng * g.r;
+  return g.g2_off + (long long)p->ngs * p->ngs * g.r;
 }
 
 // Eq. (2.10) in FP64 on the GPU for the candidate bins: T_abc = sum_x i_a i_b i_c.
 bsp_status count_triangles(bsp_plan* p, const std::vector<int>& ca, const std::vector<int>& cb,
                            const std::vector<int>& cc, std::vector<double>& tsum, cudaStream_t s) {
-  const int lxy = fft_lines_for(p->ng, BSP_FP64);
-  const int lz = fft_lines_for(p->ng / 2, BSP_FP64);
+  const int lxy = fft_lines_for(p->ngs, BSP_FP64);
+  const int lz = fft_lines_for(p->ngs / 2, BSP_FP64);
   std::vector<Item> xi, yi, zi;
   make_items(p, lxy, lz, xi, yi, zi);
   std::vector<void*> tmp;
@@ -386,14 +421,14 @@ bsp_status count_triangles(bsp_plan* p, const std::vector<int>& ca, const std::v
   Item *dxi = nullptr, *dyi = nullptr, *dzi = nullptr;
   bsp_status st;
 #define TRY(x) do { st = (x); if (st != BSP_OK) { cleanup(); return st; } } while (0)
-  TRY(dev_alloc(p, p->ng * sizeof(double2), &tw)); tmp.push_back(tw);
+  TRY(dev_alloc(p, p->ngs * sizeof(double2), &tw)); tmp.push_back(tw);
   TRY(dev_alloc(p, g1_elems(p) * sizeof(double2), &g1)); tmp.push_back(g1);
   TRY(dev_alloc(p, g2_elems(p) * sizeof(double2), &g2)); tmp.push_back(g2);
   TRY(dev_alloc(p, (size_t)p->ns * p->nvox() * sizeof(double), &f)); tmp.push_back(f);
   TRY(dev_upload(p, xi, &dxi, s)); tmp.push_back(dxi);
   TRY(dev_upload(p, yi, &dyi, s)); tmp.push_back(dyi);
   TRY(dev_upload(p, zi, &dzi, s)); tmp.push_back(dzi);
-  TRY(launch_twiddles<double>(tw, p->ng, s));
+  TRY(launch_twiddles<double>(tw, p->ngs, s));
   TRY(run_passes<double>(p, nullptr, 0, tw, g1, g2, f, dxi, (int)xi.size(), dyi, (int)yi.size(), dzi,
                          (int)zi.size(), lxy, lz, s));
   std::vector<int2> pairs;
@@ -419,6 +454,7 @@ bsp_status count_triangles(bsp_plan* p, const std::vector<int>& ca, const std::v
   c.partial = static_cast<double*>(part);
   c.msum = static_cast<double*>(ms);
   c.n_out = (int)ca.size();
+  c.scale = 1.0;  // scaled to the ng^3 grid on the host
   TRY(launch_contract_simt<double>(c, s));
   TRY(launch_reduce_partials(c, s));
   tsum.assign(ca.size(), 0.0);
@@ -450,7 +486,7 @@ bsp_status run_contract(bsp_plan* p, const void* fields, double* msum, cudaStrea
     st = launch_contract_tc(a, s);
     if (st != BSP_OK) return st;
     if (mid) BSP_CUDA(cudaEventRecord(mid, s));
-    return launch_reduce_tc(a, p->d_tc_map, (int)p->trips.size(), msum, s);
+    return launch_reduce_tc(a, p->d_tc_map, (int)p->trips.size(), msum, p->sum_scale, s);
   }
   ContractArgs c{};
   c.fields = fields;
@@ -464,6 +500,7 @@ bsp_status run_contract(bsp_plan* p, const void* fields, double* msum, cudaStrea
   c.partial = p->partial;
   c.msum = msum;
   c.n_out = (int)p->trips.size();
+  c.scale = p->sum_scale;
   st = launch_contract_simt<T>(c, s);
   if (st != BSP_OK) return st;
   if (mid) BSP_CUDA(cudaEventRecord(mid, s));
@@ -482,6 +519,7 @@ bsp_status plan_passes(bsp_plan* p, const void* spec, void* fields, cudaStream_t
   a.tw = p->tw;
   a.geom = p->d_geom;
   a.ng = p->ng;
+  a.ngs = p->ngs;
   a.rsd = p->rsd;
   a.beta = p->beta;
   a.rmax = p->rmax;
@@ -495,7 +533,7 @@ bsp_status plan_passes(bsp_plan* p, const void* spec, void* fields, cudaStream_t
     st = launch_warp_ypass(a, p->nwyi, s);
     if (st != BSP_OK) return st;
     if (ev) BSP_CUDA(cudaEventRecord(ev[1], s));
-    st = launch_warp_zpass(a, (long long)p->ns * p->ng * p->ng, p->n_sm, s);
+    st = launch_warp_zpass(a, (long long)p->ns * p->ngs * p->ngs, p->n_sm, s);
     if (st != BSP_OK) return st;
     if (ev) BSP_CUDA(cudaEventRecord(ev[2], s));
     return BSP_OK;
@@ -552,7 +590,7 @@ bsp_status estimate_impl(bsp_plan* p, const void* spec, double* b_trip, double* 
 void stage_work(const bsp_plan* p, double* bytes, double* flops) {
   const double ce = 2.0 * p->elem();
   const double re = (double)p->elem();
-  const double ng = (double)p->ng;
+  const double ng = (double)p->ngs;
   for (int i = 0; i < BSP_N_STAGES; ++i) { bytes[i] = 0.0; flops[i] = 0.0; }
   for (int n = 0; n < p->ns; ++n) {
     const ShellGeom& g = p->geom[n];
@@ -620,7 +658,8 @@ bsp_status bsp_plan_create(const bsp_plan_desc* desc, void* stream, bsp_plan** o
   std::vector<double> tsum;
   st = count_triangles(p, ca, cb, cc, tsum, s);
   if (st != BSP_OK) { bsp_plan_destroy(p); return st; }
-  const double ng3 = (double)p->nvox();
+  for (double& t : tsum) t *= p->sum_scale;  // sums over the ng^3 grid (exact up to rounding)
+  const double ng3 = (double)p->ng * (double)p->ng * (double)p->ng;
   std::vector<int> ka, kb, kc;
   std::vector<double> kt;
   for (size_t i = 0; i < ca.size(); ++i) {
@@ -650,8 +689,8 @@ bsp_status bsp_plan_create(const bsp_plan_desc* desc, void* stream, bsp_plan** o
     p->trips.push_back(t);
   }
   // estimator buffers in the plan's precision
-  p->lines_xy = fft_lines_for(p->ng, p->prec);
-  p->lines_z = fft_lines_for(p->ng / 2, p->prec);
+  p->lines_xy = fft_lines_for(p->ngs, p->prec);
+  p->lines_z = fft_lines_for(p->ngs / 2, p->prec);
   std::vector<Item> xi, yi, zi;
   make_items(p, p->lines_xy, p->lines_z, xi, yi, zi);
   p->nxi = (int)xi.size(); p->nyi = (int)yi.size(); p->nzi = (int)zi.size();
@@ -675,13 +714,13 @@ bsp_status bsp_plan_create(const bsp_plan_desc* desc, void* stream, bsp_plan** o
     }
   }
 #define TRY(x) do { st = (x); if (st != BSP_OK) { bsp_plan_destroy(p); return st; } } while (0)
-  TRY(dev_alloc(p, p->ng * ce, &p->tw));
-  TRY(p->prec == BSP_FP64 ? launch_twiddles<double>(p->tw, p->ng, s) : launch_twiddles<float>(p->tw, p->ng, s));
+  TRY(dev_alloc(p, p->ngs * ce, &p->tw));
+  TRY(p->prec == BSP_FP64 ? launch_twiddles<double>(p->tw, p->ngs, s) : launch_twiddles<float>(p->tw, p->ngs, s));
   TRY(dev_upload(p, xi, &p->d_xi, s));
   TRY(dev_upload(p, yi, &p->d_yi, s));
   TRY(dev_upload(p, zi, &p->d_zi, s));
   for (const ShellGeom& g : p->geom) p->rmax = std::max(p->rmax, g.r);
-  p->warp_fft = p->prec != BSP_FP64 && warp_fft_supported(p->ng);
+  p->warp_fft = p->prec != BSP_FP64 && warp_fft_supported(p->ngs);
   if (p->warp_fft) {
     std::vector<Item> wx, wy, wz;
     make_items(p, warp_fft_lines(), 1, wx, wy, wz);
@@ -759,6 +798,12 @@ bsp_status bsp_plan_info(const bsp_plan* p, int* n_triplets, int* n_shells, size
   if (n_shells) *n_shells = p->ns;
   if (field_bytes) *field_bytes = p->field_bytes();
   if (device_bytes) *device_bytes = p->dev_bytes;
+  return BSP_OK;
+}
+
+bsp_status bsp_plan_grid(const bsp_plan* p, int* ng_eval) {
+  if (!p || !ng_eval) return fail(BSP_ERR_INVALID_ARG, "NULL argument");
+  *ng_eval = p->ngs;
   return BSP_OK;
 }
 

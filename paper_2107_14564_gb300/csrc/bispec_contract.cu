@@ -87,7 +87,7 @@ contract_simt_kernel(ContractArgs a, long long vox_per_block) {
   }
 }
 
-// msum[map[tile][k]] = sum over blocks of partial[block][tile][k], blocks in order.
+// msum[map[tile][k]] = scale * sum over blocks of partial[block][tile][k], blocks in order.
 __global__ void reduce_partials_kernel(ContractArgs a) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= a.ntiles * 16) return;
@@ -95,7 +95,7 @@ __global__ void reduce_partials_kernel(ContractArgs a) {
   if (dst < 0) return;
   double s = 0.0;
   for (int b = 0; b < a.gridx; ++b) s += a.partial[(long long)b * a.ntiles * 16 + idx];
-  a.msum[dst] = s;
+  a.msum[dst] = a.scale * s;
 }
 
 template <typename T>

@@ -91,13 +91,14 @@ __global__ void __launch_bounds__(kFftThreads) xpass_kernel(PassArgs a, int max_
   using C = cplx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
-  const int ng = a.ng;
-  C* tws = buf + (size_t)max_lines * ng;
+  const int ng = a.ng;   // input spectrum grid
+  const int S = a.ngs;   // evaluation grid: line length
+  C* tws = buf + (size_t)max_lines * S;
   const Item it = a.items[blockIdx.x];
   const ShellGeom g = a.geom[it.n];
   const int nl = it.cnt;
-  load_twiddles<T>(tws, a.tw, ng);
-  for (int i = threadIdx.x; i < nl * ng; i += blockDim.x) buf[i] = c_make<C>(T(0), T(0));
+  load_twiddles<T>(tws, a.tw, S);
+  for (int i = threadIdx.x; i < nl * S; i += blockDim.x) buf[i] = c_make<C>(T(0), T(0));
   __syncthreads();
   const int r = g.r;
   const int w = 2 * r - 1;
@@ -117,17 +118,17 @@ __global__ void __launch_bounds__(kFftThreads) xpass_kernel(PassArgs a, int max_
         const T fac = T(1.0 + a.beta * (double)(kz * kz) / (double)q);
         val = c_scale(val, fac);
       }
-      buf[kzl * ng + ix] = val;
+      buf[kzl * S + (mx < 0 ? mx + S : mx)] = val;
     }
   }
   __syncthreads();
-  fft_lines<T>(buf, nl, ng, a.st, tws, 1);
+  fft_lines<T>(buf, nl, S, a.st, tws, 1);
   const int jy = ky + r - 1;
   C* g1 = static_cast<C*>(a.g1) + g.g1_off;
-  for (int idx = threadIdx.x; idx < ng * nl; idx += blockDim.x) {
+  for (int idx = threadIdx.x; idx < S * nl; idx += blockDim.x) {
     const int kzl = idx % nl;
     const int x = idx / nl;
-    g1[((long long)x * w + jy) * r + it.v0 + kzl] = buf[kzl * ng + x];
+    g1[((long long)x * w + jy) * r + it.v0 + kzl] = buf[kzl * S + x];
   }
 }
 
@@ -137,7 +138,7 @@ __global__ void __launch_bounds__(kFftThreads) ypass_kernel(PassArgs a, int max_
   using C = cplx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
-  const int ng = a.ng;
+  const int ng = a.ngs;  // evaluation grid
   C* tws = buf + (size_t)max_lines * ng;
   const Item it = a.items[blockIdx.x];
   const ShellGeom g = a.geom[it.n];
@@ -179,7 +180,7 @@ __global__ void __launch_bounds__(kFftThreads) zpass_kernel(PassArgs a, int max_
   using C = cplx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
-  const int ng = a.ng;
+  const int ng = a.ngs;  // evaluation grid
   const int M = ng / 2;
   C* tws = buf + (size_t)max_lines * M;
   const Item it = a.items[blockIdx.x];
@@ -239,7 +240,7 @@ template <typename T, typename K>
 static bsp_status launch_pass(K kernel, const PassArgs& a, int n_items, int lines, int len,
                               cudaStream_t s) {
   if (n_items == 0) return BSP_OK;
-  const size_t smem = pass_smem<T>(lines, len, a.ng);
+  const size_t smem = pass_smem<T>(lines, len, a.ngs);
   BSP_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   kernel<<<n_items, kFftThreads, smem, s>>>(a, lines);
   BSP_CUDA(cudaGetLastError());
@@ -248,15 +249,15 @@ static bsp_status launch_pass(K kernel, const PassArgs& a, int n_items, int line
 
 template <typename T>
 bsp_status launch_xpass(const PassArgs& a, int n_items, int lines, cudaStream_t s) {
-  return launch_pass<T>(xpass_kernel<T>, a, n_items, lines, a.ng, s);
+  return launch_pass<T>(xpass_kernel<T>, a, n_items, lines, a.ngs, s);
 }
 template <typename T>
 bsp_status launch_ypass(const PassArgs& a, int n_items, int lines, cudaStream_t s) {
-  return launch_pass<T>(ypass_kernel<T>, a, n_items, lines, a.ng, s);
+  return launch_pass<T>(ypass_kernel<T>, a, n_items, lines, a.ngs, s);
 }
 template <typename T>
 bsp_status launch_zpass(const PassArgs& a, int n_items, int lines, cudaStream_t s) {
-  return launch_pass<T>(zpass_kernel<T>, a, n_items, lines, a.ng / 2, s);
+  return launch_pass<T>(zpass_kernel<T>, a, n_items, lines, a.ngs / 2, s);
 }
 template <typename T>
 bsp_status launch_twiddles(void* tw, int ng, cudaStream_t s) {

@@ -19,23 +19,24 @@
 namespace bsp {
 namespace {
 
-constexpr int kLines = 16;          // lines per X/Y block (one per warp)
-constexpr int kXYThreads = kLines * 32;
+constexpr int kLines = 16;          // lines per X/Y block
 constexpr int kZThreads = 256;      // 8 warps, one line at a time each
 constexpr int kTileLd = kLines + 1; // padded tile row (complex)
 
 __device__ __forceinline__ int padi(int i) { return i + (i >> 3); }
 
-// Radix list of a power-of-two length with 32 lanes (every stage uses radix <= points/lane).
+// Radix list and lanes per line of each supported length: every radix divides the points per
+// lane E = N / LPL, so each lane runs E / R whole butterflies per stage.
 template <int N> struct Radices;
-template <> struct Radices<64> { static constexpr int n = 3; static constexpr int r[3] = {4, 4, 4}; };
-template <> struct Radices<128> { static constexpr int n = 4; static constexpr int r[4] = {4, 4, 4, 2}; };
-template <> struct Radices<256> { static constexpr int n = 3; static constexpr int r[3] = {8, 8, 4}; };
-template <> struct Radices<512> { static constexpr int n = 3; static constexpr int r[3] = {8, 8, 8}; };
-template <> struct Radices<1024> { static constexpr int n = 4; static constexpr int r[4] = {8, 8, 8, 2}; };
-
-template <int N> struct LanesPerLine { static constexpr int value = 32; };
-template <> struct LanesPerLine<64> { static constexpr int value = 16; };
+template <> struct Radices<64> { static constexpr int lpl = 16, n = 3; static constexpr int r[3] = {4, 4, 4}; };
+template <> struct Radices<96> { static constexpr int lpl = 8, n = 4; static constexpr int r[4] = {3, 4, 4, 2}; };
+template <> struct Radices<128> { static constexpr int lpl = 32, n = 4; static constexpr int r[4] = {4, 4, 4, 2}; };
+template <> struct Radices<192> { static constexpr int lpl = 16, n = 4; static constexpr int r[4] = {3, 4, 4, 4}; };
+template <> struct Radices<256> { static constexpr int lpl = 32, n = 3; static constexpr int r[3] = {8, 8, 4}; };
+template <> struct Radices<384> { static constexpr int lpl = 32, n = 5; static constexpr int r[5] = {3, 4, 4, 4, 2}; };
+template <> struct Radices<512> { static constexpr int lpl = 32, n = 3; static constexpr int r[3] = {8, 8, 8}; };
+template <> struct Radices<768> { static constexpr int lpl = 32, n = 4; static constexpr int r[4] = {3, 8, 8, 4}; };
+template <> struct Radices<1024> { static constexpr int lpl = 32, n = 4; static constexpr int r[4] = {8, 8, 8, 2}; };
 
 // One Stockham stage of radix R after sub-transforms of length NS; v[b R + r] is input r of
 // butterfly j = lane + b LPL. tw[t * TWS] = exp(2 pi i t / N).
@@ -46,7 +47,7 @@ __device__ __forceinline__ void stage_compute(float2* v, int lane, const float2*
 #pragma unroll
   for (int b = 0; b < BPL; ++b) {
     const int j = lane + b * LPL;
-    const int k = j & (NS - 1);
+    const int k = j % NS;
     if (NS > 1) {
 #pragma unroll
       for (int r = 1; r < R; ++r) v[b * R + r] = c_mul(v[b * R + r], tw[r * k * TU * TWS]);
@@ -61,7 +62,7 @@ __device__ __forceinline__ void stage_store(float2* buf, const float2* v, int la
 #pragma unroll
   for (int b = 0; b < BPL; ++b) {
     const int j = lane + b * LPL;
-    const int k = j & (NS - 1);
+    const int k = j % NS;
     const int d = (j - k) * R + k;
 #pragma unroll
     for (int r = 0; r < R; ++r) buf[padi(d + r * NS)] = v[b * R + r];
@@ -99,33 +100,39 @@ template <int N> __host__ __device__ constexpr int first_radix() { return Radice
 template <int N> __host__ __device__ constexpr int last_radix() { return Radices<N>::r[Radices<N>::n - 1]; }
 
 // ---------------------------------------------------------------- X and Y passes
-// XPASS: lines along x at (shell n, k_y = it.u, k_z = it.v0 ..), input the half spectrum
-//        (shell mask and optional Kaiser factor applied on load), output G1[x][k_y][k_z].
+// XPASS: lines along x at (shell n, k_y = it.u, k_z = it.v0 ..), input the half spectrum of the
+//        Ng grid (shell mask and optional Kaiser factor applied on load), output G1[x][k_y][k_z].
 // else : lines along y at (shell n, x = it.u, k_z = it.v0 ..), input G1, output G2[x][y][k_z].
+// N is the side of the evaluation grid (the transform length); kLines lines per block.
+template <int N> struct XY {
+  static constexpr int kLpl = Radices<N>::lpl;
+  static constexpr int kThreads = kLines * kLpl;
+};
+
 template <int N, bool XPASS>
-__global__ void __launch_bounds__(kXYThreads) xy_warp_kernel(PassArgs a) {
-  constexpr int LPL = 32;
+__global__ void __launch_bounds__(XY<N>::kThreads) xy_warp_kernel(PassArgs a) {
+  constexpr int LPL = XY<N>::kLpl;
+  constexpr int NT = XY<N>::kThreads;
   constexpr int E = N / LPL;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* tw = reinterpret_cast<float2*>(smem_raw);            // N
-  float2* bufs = tw + N;                                         // kLines x padi(N)
   constexpr int kBufLd = N + N / 8;
-  float2* tile = bufs + (size_t)kLines * kBufLd;                 // (2r-1) x kTileLd
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* tw = reinterpret_cast<float2*>(smem_raw);  // N entries exp(2 pi i t / N)
+  float2* bufs = tw + N;                               // kLines x kBufLd
+  float2* tile = bufs + (size_t)kLines * kBufLd;       // (2r-1) x kTileLd
   const Item it = a.items[blockIdx.x];
   const ShellGeom g = a.geom[it.n];
   const int r = g.r;
   const int w = 2 * r - 1;
   const int tid = threadIdx.x;
-  const int warp = tid >> 5;
-  const int lane = tid & 31;
-  for (int i = tid; i < N; i += kXYThreads) tw[i] = static_cast<const float2*>(a.tw)[i];
+  for (int i = tid; i < N; i += NT) tw[i] = static_cast<const float2*>(a.tw)[i];
   // ---- input tile [row = k + r - 1][line]
   if (XPASS) {
     const float2* spec = static_cast<const float2*>(a.spec);
+    const int ng = a.ng;  // side of the input spectrum's grid
     const int ky = it.u;
-    const int iy = ky < 0 ? ky + N : ky;
-    const int hz = N / 2 + 1;
-    for (int idx = tid; idx < w * kLines; idx += kXYThreads) {
+    const int iy = ky < 0 ? ky + ng : ky;
+    const int hz = ng / 2 + 1;
+    for (int idx = tid; idx < w * kLines; idx += NT) {
       const int l = idx & (kLines - 1);
       const int row = idx >> 4;
       const int mx = row - (r - 1);
@@ -133,8 +140,8 @@ __global__ void __launch_bounds__(kXYThreads) xy_warp_kernel(PassArgs a) {
       const int q = mx * mx + ky * ky + kz * kz;
       float2 val = make_float2(0.f, 0.f);
       if (l < it.cnt && q >= g.qlo && q < g.qhi) {
-        const int ix = mx < 0 ? mx + N : mx;
-        val = spec ? spec[((long long)ix * N + iy) * hz + kz] : make_float2(1.f, 0.f);
+        const int ix = mx < 0 ? mx + ng : mx;
+        val = spec ? spec[((long long)ix * ng + iy) * hz + kz] : make_float2(1.f, 0.f);
         if (a.rsd) {
           const float fac = (float)(1.0 + a.beta * (double)(kz * kz) / (double)q);
           val.x *= fac;
@@ -146,7 +153,7 @@ __global__ void __launch_bounds__(kXYThreads) xy_warp_kernel(PassArgs a) {
   } else {
     const float2* g1 = static_cast<const float2*>(a.g1) + g.g1_off;
     const int x = it.u;
-    for (int idx = tid; idx < w * kLines; idx += kXYThreads) {
+    for (int idx = tid; idx < w * kLines; idx += NT) {
       const int l = idx & (kLines - 1);
       const int row = idx >> 4;
       const int ky = row - (r - 1);
@@ -157,12 +164,13 @@ __global__ void __launch_bounds__(kXYThreads) xy_warp_kernel(PassArgs a) {
     }
   }
   __syncthreads();
-  // ---- one line per warp
+  // ---- one line per LPL lanes
   {
     constexpr int R1 = first_radix<N>();
     constexpr int BPL = N / (R1 * LPL);
+    const int l = tid / LPL;
+    const int lane = tid & (LPL - 1);
     float2 v[E];
-    const int l = warp;
 #pragma unroll
     for (int b = 0; b < BPL; ++b)
 #pragma unroll
@@ -172,7 +180,7 @@ __global__ void __launch_bounds__(kXYThreads) xy_warp_kernel(PassArgs a) {
         const int row = k + r - 1;
         v[b * R1 + rr] = (row >= 0 && row < w) ? tile[row * kTileLd + l] : make_float2(0.f, 0.f);
       }
-    float2* buf = bufs + (size_t)warp * kBufLd;
+    float2* buf = bufs + (size_t)l * kBufLd;
     warp_fft_from<N, LPL, 0, 1, 1>(v, buf, lane, tw);
     constexpr int RL = last_radix<N>();
     constexpr int BPLL = N / (RL * LPL);
@@ -193,7 +201,7 @@ __global__ void __launch_bounds__(kXYThreads) xy_warp_kernel(PassArgs a) {
     out = static_cast<float2*>(a.g2) + g.g2_off + (long long)it.u * N * r + it.v0;
     row_stride = r;
   }
-  for (int idx = tid; idx < N * kLines; idx += kXYThreads) {
+  for (int idx = tid; idx < N * kLines; idx += NT) {
     const int l = idx & (kLines - 1);
     const int y = idx >> 4;
     if (l < it.cnt) out[y * row_stride + l] = bufs[(size_t)l * kBufLd + padi(y)];
@@ -201,25 +209,26 @@ __global__ void __launch_bounds__(kXYThreads) xy_warp_kernel(PassArgs a) {
 }
 
 // ---------------------------------------------------------------- Z pass
-// Lines (shell n, x, y) in order; each warp takes lines warp_id, warp_id + warps, ...
-template <int NG>
+// Lines (shell n, x, y) of the S^3 evaluation grid in order; each group of LPL lanes takes
+// lines id, id + groups, ...
+template <int S>
 __global__ void __launch_bounds__(kZThreads) z_warp_kernel(PassArgs a, long long n_lines) {
-  constexpr int M = NG / 2;
-  constexpr int LPL = LanesPerLine<M>::value;
+  constexpr int M = S / 2;
+  constexpr int LPL = Radices<M>::lpl;
   constexpr int LPW = 32 / LPL;  // lines per warp at a time
   constexpr int E = M / LPL;
   constexpr int kBufLd = M + M / 8;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* tw = reinterpret_cast<float2*>(smem_raw);  // NG entries exp(2 pi i t / NG)
-  float2* bufs = tw + NG;
+  float2* tw = reinterpret_cast<float2*>(smem_raw);  // S entries exp(2 pi i t / S)
+  float2* bufs = tw + S;
   const int tid = threadIdx.x;
-  for (int i = tid; i < NG; i += kZThreads) tw[i] = static_cast<const float2*>(a.tw)[i];
+  for (int i = tid; i < S; i += kZThreads) tw[i] = static_cast<const float2*>(a.tw)[i];
   __syncthreads();
   const int warp = tid >> 5;
   const int sub = (tid & 31) / LPL;  // line slot inside the warp
   const int lane = tid & (LPL - 1);
   float2* buf = bufs + (size_t)(warp * LPW + sub) * kBufLd;
-  const long long plane = (long long)NG * NG;
+  const long long plane = (long long)S * S;
   const long long stride = (long long)gridDim.x * (kZThreads / 32) * LPW;
   constexpr int R1 = first_radix<M>();
   constexpr int BPL = M / (R1 * LPL);
@@ -240,12 +249,12 @@ __global__ void __launch_bounds__(kZThreads) z_warp_kernel(PassArgs a, long long
         const int k = lane + b * LPL + rr * (M / R1);
         const float2 xk = k < r ? src[k] : make_float2(0.f, 0.f);
         const float2 xm = (k > 0 && M - k < r) ? src[M - k] : make_float2(0.f, 0.f);
-        const float2 e = make_float2(xk.x + xm.x, xk.y - xm.y);          // X[k] + conj X[M-k]
+        const float2 e = make_float2(xk.x + xm.x, xk.y - xm.y);                // X[k] + conj X[M-k]
         const float2 o = c_mul(make_float2(xk.x - xm.x, xk.y + xm.y), tw[k]);  // (X[k] - conj X[M-k]) W^k
-        v[b * R1 + rr] = make_float2(e.x - o.y, e.y + o.x);              // e + i o
+        v[b * R1 + rr] = make_float2(e.x - o.y, e.y + o.x);                    // e + i o
       }
     warp_fft_from<M, LPL, 0, 1, 2>(v, buf, lane, tw);
-    float2* dst = reinterpret_cast<float2*>(static_cast<float*>(a.fields) + (long long)n * NG * plane + xy * NG);
+    float2* dst = reinterpret_cast<float2*>(static_cast<float*>(a.fields) + (long long)n * S * plane + xy * S);
 #pragma unroll
     for (int b = 0; b < BPLL; ++b)
 #pragma unroll
@@ -257,62 +266,63 @@ template <int N, bool XPASS>
 bsp_status launch_xy(const PassArgs& a, int n_items, cudaStream_t s) {
   if (n_items == 0) return BSP_OK;
   // the tile holds 2 r - 1 rows of the largest shell
-  const int rmax = a.rmax;
-  const size_t smem = ((size_t)N + (size_t)kLines * (N + N / 8) + (size_t)(2 * rmax) * kTileLd) * sizeof(float2);
+  const size_t smem =
+      ((size_t)N + (size_t)kLines * (N + N / 8) + (size_t)(2 * a.rmax) * kTileLd) * sizeof(float2);
   BSP_CUDA(cudaFuncSetAttribute(xy_warp_kernel<N, XPASS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  xy_warp_kernel<N, XPASS><<<n_items, kXYThreads, smem, s>>>(a);
+  xy_warp_kernel<N, XPASS><<<n_items, XY<N>::kThreads, smem, s>>>(a);
   BSP_CUDA(cudaGetLastError());
   return BSP_OK;
 }
 
-template <int NG>
+template <int S>
 bsp_status launch_z(const PassArgs& a, long long n_lines, int n_sm, cudaStream_t s) {
-  constexpr int M = NG / 2;
-  constexpr int LPW = 32 / LanesPerLine<M>::value;
-  const size_t smem = ((size_t)NG + (size_t)(kZThreads / 32) * LPW * (M + M / 8)) * sizeof(float2);
-  BSP_CUDA(cudaFuncSetAttribute(z_warp_kernel<NG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  constexpr int M = S / 2;
+  constexpr int LPW = 32 / Radices<M>::lpl;
+  const size_t smem = ((size_t)S + (size_t)(kZThreads / 32) * LPW * (M + M / 8)) * sizeof(float2);
+  BSP_CUDA(cudaFuncSetAttribute(z_warp_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
-  BSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, z_warp_kernel<NG>, kZThreads, smem));
+  BSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, z_warp_kernel<S>, kZThreads, smem));
   long long blocks = (long long)std::max(per_sm, 1) * n_sm;
   const long long need = (n_lines + (kZThreads / 32) * LPW - 1) / ((kZThreads / 32) * LPW);
   if (blocks > need) blocks = need;
   if (blocks < 1) blocks = 1;
-  z_warp_kernel<NG><<<(unsigned)blocks, kZThreads, smem, s>>>(a, n_lines);
+  z_warp_kernel<S><<<(unsigned)blocks, kZThreads, smem, s>>>(a, n_lines);
   BSP_CUDA(cudaGetLastError());
   return BSP_OK;
 }
 
 }  // namespace
 
-bool warp_fft_supported(int ng) { return ng == 128 || ng == 256 || ng == 512 || ng == 1024; }
+bool warp_fft_supported(int s) {
+  return s == 128 || s == 192 || s == 256 || s == 384 || s == 512 || s == 768 || s == 1024;
+}
 int warp_fft_lines() { return kLines; }
 
+#define BSP_WARP_SIZES(X) X(128) X(192) X(256) X(384) X(512) X(768) X(1024)
+
 bsp_status launch_warp_xpass(const PassArgs& a, int n_items, cudaStream_t s) {
-  switch (a.ng) {
-    case 128: return launch_xy<128, true>(a, n_items, s);
-    case 256: return launch_xy<256, true>(a, n_items, s);
-    case 512: return launch_xy<512, true>(a, n_items, s);
-    case 1024: return launch_xy<1024, true>(a, n_items, s);
+  switch (a.ngs) {
+#define X(S) case S: return launch_xy<S, true>(a, n_items, s);
+    BSP_WARP_SIZES(X)
+#undef X
   }
   return fail_c(BSP_ERR_NOT_SUPPORTED, "warp FFT: unsupported grid");
 }
 
 bsp_status launch_warp_ypass(const PassArgs& a, int n_items, cudaStream_t s) {
-  switch (a.ng) {
-    case 128: return launch_xy<128, false>(a, n_items, s);
-    case 256: return launch_xy<256, false>(a, n_items, s);
-    case 512: return launch_xy<512, false>(a, n_items, s);
-    case 1024: return launch_xy<1024, false>(a, n_items, s);
+  switch (a.ngs) {
+#define X(S) case S: return launch_xy<S, false>(a, n_items, s);
+    BSP_WARP_SIZES(X)
+#undef X
   }
   return fail_c(BSP_ERR_NOT_SUPPORTED, "warp FFT: unsupported grid");
 }
 
 bsp_status launch_warp_zpass(const PassArgs& a, long long n_lines, int n_sm, cudaStream_t s) {
-  switch (a.ng) {
-    case 128: return launch_z<128>(a, n_lines, n_sm, s);
-    case 256: return launch_z<256>(a, n_lines, n_sm, s);
-    case 512: return launch_z<512>(a, n_lines, n_sm, s);
-    case 1024: return launch_z<1024>(a, n_lines, n_sm, s);
+  switch (a.ngs) {
+#define X(S) case S: return launch_z<S>(a, n_lines, n_sm, s);
+    BSP_WARP_SIZES(X)
+#undef X
   }
   return fail_c(BSP_ERR_NOT_SUPPORTED, "warp FFT: unsupported grid");
 }

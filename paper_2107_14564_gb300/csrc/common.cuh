@@ -66,16 +66,17 @@ struct PassArgs {
   const void* tw;         // twiddles exp(+2 pi i j / ng), j < ng (complex T)
   const ShellGeom* geom;  // per shell
   const Item* items;      // work items of this pass
-  int ng;
+  int ng;                 // side of the input spectrum's grid
+  int ngs;                // side of the evaluation grid (transform length), <= ng
   int rsd;
   double beta;
   FftStages st;           // stage list of this pass's line length
   int rmax;               // largest r of all shells
 };
 
-// Warp-per-line FP32 passes (bispec_fft_warp.cu) for power-of-two grids 128..1024; X/Y items
-// hold at most warp_fft_lines() lines.
-bool warp_fft_supported(int ng);
+// Warp-per-line FP32 passes (bispec_fft_warp.cu) for evaluation grids 2^p and 3 * 2^p from
+// 128 to 1024; X/Y items hold at most warp_fft_lines() lines.
+bool warp_fft_supported(int ngs);
 int warp_fft_lines();
 bsp_status launch_warp_xpass(const PassArgs& a, int n_items, cudaStream_t s);
 bsp_status launch_warp_ypass(const PassArgs& a, int n_items, cudaStream_t s);
@@ -121,6 +122,7 @@ struct ContractArgs {
   int gridx;
   double* msum;           // [n_out]
   int n_out;
+  double scale;           // msum = scale * (sum over the evaluation grid)
 };
 template <typename T>
 bsp_status launch_contract_simt(const ContractArgs& a, cudaStream_t s);
@@ -156,7 +158,8 @@ struct TcArgs {
 int tc_padded_shells(int ns);
 size_t tc_partial_doubles(int n_mtiles, int gridy, int np);
 bsp_status launch_contract_tc(const TcArgs& a, cudaStream_t s);
-// msum[t] = sum_y partial[y][map[t]], map[t] = (mtile * 128 + row) * np + c of bin t
-bsp_status launch_reduce_tc(const TcArgs& a, const int* map, int n_out, double* msum, cudaStream_t s);
+// msum[t] = scale * sum_y partial[y][map[t]], map[t] = (mtile * 128 + row) * np + c of bin t
+bsp_status launch_reduce_tc(const TcArgs& a, const int* map, int n_out, double* msum, double scale,
+                            cudaStream_t s);
 
 }  // namespace bsp

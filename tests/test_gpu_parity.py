@@ -116,8 +116,8 @@ def test_shell_fields_parity(lib, prec):
     c64 = prec != "fp64"
     spec = _spec(ng, 1.5, 0.1, 4, c64=c64)
     pl = P.make_plan(ng, float(ng), edges)
-    want = fbe.shell_fields(spec.astype(np.complex128), pl)
     gp = lib.Plan(ng, float(ng), edges, precision=prec)
+    want = fbe.shell_fields_on_grid(spec.astype(np.complex128), pl, gp.ng_eval)
     got = gp.shell_fields(torch.from_numpy(spec).cuda()).cpu().numpy()
     tol = 1e-12 if prec == "fp64" else 2e-6
     for n in range(pl.ns):
@@ -146,16 +146,18 @@ def test_fp32_parity_ragged(lib, prec):
 
 
 def test_contract_on_oracle_fields(lib):
-    """The contraction alone, fed the oracle's FP64 fields."""
+    """The contraction alone, fed the oracle's FP64 fields sampled on the plan's evaluation grid;
+    its sums must equal the oracle's sums over the full Ng^3 grid (the coarser grid is exact)."""
     ng = 32
     edges = _edges(ng, 8)
     spec = _spec(ng, 2.0, 0.1, 6, c64=False)
     pl, res = _oracle(spec, ng, edges)
-    fields = fbe.shell_fields(spec, pl)
-    stack = np.stack([fields[n] for n in range(pl.ns)])
     gp = lib.Plan(ng, float(ng), edges, precision="fp64")
+    assert gp.ng_eval < ng
+    fields = fbe.shell_fields_on_grid(spec, pl, gp.ng_eval)
+    stack = np.stack([fields[n] for n in range(pl.ns)])
     msum = gp.contract(torch.from_numpy(stack).cuda()).cpu().numpy()
-    assert np.max(np.abs(msum - res["msum"]) / np.abs(res["msum"])) < 1e-12
+    assert np.max(np.abs(msum - res["msum"]) / np.abs(res["msum"])) < 1e-10
 
 
 def test_host_entry_point(lib):
@@ -201,10 +203,12 @@ def test_mixed_contract_on_oracle_fields(lib):
     edges = _edges(ng, 10)
     spec = _spec(ng, 2.0, 0.1, 8, c64=False)
     pl, res = _oracle(spec, ng, edges, with_abs=True)
-    fields = fbe.shell_fields(spec, pl)
+    gp = lib.Plan(ng, float(ng), edges, precision="mixed_bf16x3")
+    size = gp.ng_eval
+    fields = fbe.shell_fields_on_grid(spec, pl, size)
     stack = np.stack([fields[n] for n in range(pl.ns)]).astype(np.float32)
     exact = fbe.triple_sums({n: stack[n].astype(np.float64) for n in range(pl.ns)}, res["triplets"])
-    gp = lib.Plan(ng, float(ng), edges, precision="mixed_bf16x3")
+    exact *= (ng / size) ** 3
     msum = gp.contract(torch.from_numpy(stack).cuda()).cpu().numpy()
     gp.check()
     assert np.max(np.abs(msum - exact) / res["asum"]) < 1e-4

@@ -147,3 +147,38 @@ def test_condition_scale_bounds_the_sum():
     spec = fieldgen.spectrum(fieldgen.quadratic_field(ng, float(ng), 2.0, 0.1, 3))
     res = fbe.estimate(spec, pl, with_abs=True)
     assert np.all(np.abs(res["msum"]) <= res["asum"] * (1 + 1e-12))
+
+
+def test_fields_on_a_coarser_grid():
+    """Shell fields sampled on a coarser S^3 grid: (i) S = Ng reproduces shell_fields; (ii) values
+    equal the plane-wave sum of Eq. (2.8) at the sample points; (iii) triple sums times (Ng/S)^3
+    equal the Ng^3 sums whenever S exceeds 3 (r_max - 1), the largest wavevector component a
+    triple product holds (the exactness the GPU plan's evaluation grid relies on)."""
+    ng = 32
+    pl = _plan(ng)                               # shells up to |m| < 8: r_max - 1 = 7
+    spec = fieldgen.spectrum(fieldgen.quadratic_field(ng, float(ng), 2.0, 0.3, 17))
+    full = fbe.shell_fields(spec, pl)
+    same = fbe.shell_fields_on_grid(spec, pl, ng)
+    for n in range(pl.ns):
+        assert np.allclose(same[n], full[n], rtol=0, atol=1e-9 * np.abs(full[n]).max())
+    size = 24                                    # > 3 * 7 = 21
+    coarse = fbe.shell_fields_on_grid(spec, pl, size)
+    modes, shell, _ = dbe.ball_modes(pl)
+    vals = dbe.full_spectrum_values(spec, modes, ng)
+    rng = np.random.default_rng(4)
+    for n in (0, 3, 7):
+        sel = shell == n
+        for _ in range(3):
+            j = rng.integers(0, size, 3)
+            x = j * (ng / size)                  # grid units of the Ng grid
+            direct = np.sum(vals[sel] * np.exp(2j * np.pi * (modes[sel] @ x) / ng))
+            assert abs(direct.imag) < 1e-6 * abs(direct) + 1e-6
+            assert abs(coarse[n][tuple(j)] - direct.real) <= 1e-9 * np.abs(coarse[n]).max()
+    trips = fbe.kept_triplets(pl)[0]
+    want = fbe.triple_sums(full, trips)
+    got = fbe.triple_sums(coarse, trips) * (ng / size) ** 3
+    assert np.max(np.abs(got - want) / np.abs(want)) < 1e-10
+    # below the bound the coarse grid aliases: S = 16 < 21 no longer reproduces every bin
+    small = fbe.shell_fields_on_grid(spec, pl, 16)
+    bad = fbe.triple_sums(small, trips) * (ng / 16) ** 3
+    assert np.max(np.abs(bad - want) / np.abs(want)) > 1e-3

@@ -47,7 +47,8 @@ def _call(lib_mod, fields, ns, nvox, trip, n, out):
 def test_noalloc_matches_plan_contraction_twice(setup):
     lib_mod, plan, fields, trip, ref, asum = setup
     n = plan.n_triplets
-    nvox = plan.ng ** 3
+    nvox = plan.ng_eval ** 3
+    scale = (plan.ng / plan.ng_eval) ** 3  # plan sums refer to the Ng^3 grid
     outs = []
     free_after = []
     for _ in range(2):
@@ -55,7 +56,7 @@ def test_noalloc_matches_plan_contraction_twice(setup):
         assert _call(lib_mod, fields, plan.n_shells, nvox, trip, n, out) == 0
         torch.cuda.synchronize()
         free_after.append(torch.cuda.mem_get_info()[0])
-        outs.append(out.cpu().numpy())
+        outs.append(out.cpu().numpy() * scale)
     for got in outs:
         assert np.all(np.isfinite(got))
         assert np.max(np.abs(got - ref) / asum) < 1e-4
@@ -66,6 +67,6 @@ def test_noalloc_matches_plan_contraction_twice(setup):
 def test_noalloc_rejects_sizes_beyond_its_scratch(setup):
     lib_mod, plan, fields, trip, _, _ = setup
     out = torch.empty(8, dtype=torch.float64, device="cuda")
-    assert _call(lib_mod, fields, plan.n_shells, plan.ng ** 3, trip, 4097, out) == 1
+    assert _call(lib_mod, fields, plan.n_shells, plan.ng_eval ** 3, trip, 4097, out) == 1
     assert b"4096" in lib_mod.load().bsp_last_error()
-    assert _call(lib_mod, fields, 65, plan.ng ** 3, trip, 8, out) == 1
+    assert _call(lib_mod, fields, 65, plan.ng_eval ** 3, trip, 8, out) == 1
