@@ -39,8 +39,8 @@ WORKLOADS = {
 }
 DTYPES = {"fp64": "f64", "fp32": "f32", "mixed_bf16x3": "bf16x3/f32"}
 STAGES = ["xpass", "ypass", "zpass", "contract", "finalize"]
-STAGE_KERNEL_SRC = {"xpass": "bispec_fft.cu", "ypass": "bispec_fft.cu", "zpass": "bispec_fft.cu",
-                    "contract": "bispec_contract.cu", "finalize": "bispec_contract.cu"}
+STAGE_KERNEL_SRC = {"xpass": "bispec_fft_warp.cu", "ypass": "bispec_fft_warp.cu", "zpass": "bispec_fft_warp.cu",
+                    "contract": "bispec_contract_tc.cu", "finalize": "bispec_contract.cu"}
 
 
 def log(*a):
@@ -299,6 +299,25 @@ def run_ours(args, w):
            "h2d_bytes_per_step": int(spec_np.nbytes),
            "d2h_bytes_per_step": int(8 * (plan.n_triplets + plan.n_shells * w["n_mu"] * w["n_t"]))}
 
+    plain = None
+    if args.precision != "fp32" and not args.no_plain and world == 1:
+        pplan = binding.Plan(w["ng"], w["box"], edges_of(w), w["n_mu"], w["n_t"],
+                             rsd=w["beta"] is not None, beta=w["beta"] or 0.0, precision="fp32")
+        for _ in range(args.warmup):
+            pplan.estimate(spec)
+        torch.cuda.synchronize()
+        k = max(3, args.steps // 2)
+        e0.record(stream)
+        for _ in range(k):
+            pplan.estimate(spec)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pms = e0.elapsed_time(e1) / k
+        plain = {"precision": "fp32", "value": pplan.n_triplets / (pms / 1000.0), "unit": "bins/s",
+                 "ms_per_step": pms, "steps": k,
+                 "speedup_of_main": round(pms / ms_max, 3)}
+        pplan.close()
+
     pk, pk_kind = peaks()
     stages = {}
     for i, name in enumerate(STAGES):
@@ -313,7 +332,22 @@ def run_ours(args, w):
     dom = max(range(5), key=lambda i: st_ms[i])
     dname = STAGES[dom]
     tdom = st_ms[dom] / 1000.0
-    if dname == "contract" and args.precision == "fp32":
+    tr = plan.triplets
+    npairs = len({(int(a), int(b)) for a, b in zip(tr["a"], tr["b"])})
+    nvox = float(plan.ng_eval) ** 3
+    if dname == "contract" and args.precision == "mixed_bf16x3":
+        # split-BF16 GEMM work: 3 MMAs x 2 flops per (pair, shell column, voxel); shell columns are
+        # padded to the MMA N of 32 (or 64)
+        ncols = 32 if plan.n_shells <= 32 else 64
+        tflop = 3 * 2 * npairs * ncols * nvox / 1e12
+        ach = tflop / tdom
+        roof = {"bound": "tensor", "kernel": "contract_tc_kernel (tcgen05 kind::f16, bf16x3)",
+                "achieved": round(ach, 2), "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
+                "frac": round(ach / pk["bf16_tflops"], 4),
+                "peak_kind": f"{pk_kind} bf16_tflops (burst, cuBLAS)",
+                "work": f"3 x 2 x {npairs} pairs x {ncols} shell columns x {plan.ng_eval}^3 voxels",
+                "traffic": ncu_traffic(dname, args.workload, args.precision)}
+    elif dname == "contract" and args.precision == "fp32":
         sm_mhz = pk.get("sm_max_mhz", 2070.0)
         alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
         ach = wf[dom] / tdom / 1e12
@@ -330,8 +364,6 @@ def run_ours(args, w):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        tr = plan.triplets
-        npairs = len({(int(a), int(b)) for a, b in zip(tr["a"], tr["b"])})
         v, secs, desc = oracle_sample(w, spec_np, plan.n_triplets, npairs)
         cpu = {"value": v, "unit": "bins/s", "cores": os.cpu_count(), "kind": "oracle", "sample": desc}
 
@@ -341,7 +373,8 @@ def run_ours(args, w):
             "dtype": DTYPES[args.precision], "data": "synthetic", "config": config_of(w, args.precision),
             "fields_per_sec": fields_per_s, "n_bins": plan.n_triplets, "roofline": roof,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(nlaunch.value), "clocks": clk,
-            "stages": stages, "plan_seconds": round(plan_s, 2)}
+            "stages": stages, "plan_seconds": round(plan_s, 2), "plain_fp32": plain,
+            "eval_grid": plan.ng_eval}
     if rank == 0:
         print(json.dumps(line), flush=True)
     plan.close()
@@ -355,7 +388,9 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp32", "mixed_bf16x3", "fp64"], default="fp32")
+    ap.add_argument("--precision", choices=["fp32", "mixed_bf16x3", "fp64"], default="mixed_bf16x3")
+    ap.add_argument("--no-plain", action="store_true",
+                    help="skip timing the plain FP32 (CUDA-core contraction) form beside the main one")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="ng512_rsd")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -143,6 +143,27 @@ BSP_API bsp_status bsp_estimate(bsp_plan* plan, const void* spec, double* b_trip
 BSP_API bsp_status bsp_estimate_host(bsp_plan* plan, const void* spec_host, double* b_triplet_host,
                              double* b_grid_host, void* stream);
 
+/* Forward DFT of a real field on the modes the plan uses: spec_out[i][j][l] = sum_x delta(x)
+ * e^{-i k.x} (the half-spectrum layout above, complex64, device, caller-owned) for every mode of
+ * the ball covered by the shells; entries outside that ball are left untouched (bsp_estimate
+ * never reads them). delta_x: device, float [ng][ng][ng]. This is the transform that takes a
+ * density field delta(x) to the Delta(k) = V_c F(k) of Eq. (2.1). FP32 and mixed plans with ng =
+ * 2^p or 3 * 2^p in [128, 1024]; else BSP_ERR_NOT_SUPPORTED. Asynchronous on `stream`. */
+BSP_API bsp_status bsp_spectrum(bsp_plan* plan, const float* delta_x, void* spec_out, void* stream);
+
+/* Adjoint of bsp_estimate: dl_ddelta[x][y][z] = dL/d delta(x) on the ng^3 grid (device, float,
+ * caller-owned) for an upstream gradient dl_db[t] = dL/dB_t of the kept bins (device, doubles),
+ * at the field whose half spectrum is `spec` (device, the input of bsp_estimate). B_t is trilinear
+ * in the shell fields (Eq. (2.7), (2.8)), so
+ *   dL/d delta(y) = sum_k [sum_n S_n(k) K(k) G^_n(k)] e^{+i k.y},
+ *   G_n = sum_t dL/dB_t V_c^3 / (V T_t) (product of the bin's other two fields), one term per
+ *   position of n in the bin, G^_n its forward DFT and K the Kaiser factor of Eq. (3.4).
+ * Shell fields are recomputed (nothing is kept from a forward call); the first call allocates
+ * the adjoint buffers (about two shell-field sets). FP32 and mixed plans whose grid sides are 2^p
+ * or 3 * 2^p in [128, 1024]; else BSP_ERR_NOT_SUPPORTED. Asynchronous on `stream`. */
+BSP_API bsp_status bsp_grad(bsp_plan* plan, const void* spec, const double* dl_db, float* dl_ddelta,
+                            void* stream);
+
 /* Per-bin numerators of the last bsp_estimate on this plan, msum[t] = sum_x d_a d_b d_c, as a
  * device pointer owned by the plan (n_triplets doubles, valid until the next call on it). */
 BSP_API bsp_status bsp_last_sums(const bsp_plan* plan, const double** msum);

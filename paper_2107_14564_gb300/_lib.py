@@ -49,6 +49,8 @@ SIGNATURES = {
     "bsp_contract": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "bsp_estimate": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "bsp_estimate_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "bsp_spectrum": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "bsp_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "bsp_last_sums": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p)]),
     "bsp_plan_check": (C.c_int, [C.c_void_p, C.c_void_p]),
     "bsp_timing_enable": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),

@@ -87,6 +87,16 @@ def bsp_estimate_host(handle, spec_host, b_triplet_host, b_grid_host, stream=Non
                                         C.c_void_p(_stream_ptr(stream))))
 
 
+def bsp_spectrum(handle, delta_x: torch.Tensor, spec_out: torch.Tensor, stream=None) -> None:
+    check(_lib.load().bsp_spectrum(handle, C.c_void_p(_ptr(delta_x)), C.c_void_p(_ptr(spec_out)),
+                                   C.c_void_p(_stream_ptr(stream))))
+
+
+def bsp_grad(handle, spec: torch.Tensor, dl_db: torch.Tensor, dl_ddelta: torch.Tensor, stream=None) -> None:
+    check(_lib.load().bsp_grad(handle, C.c_void_p(_ptr(spec)), C.c_void_p(_ptr(dl_db)),
+                               C.c_void_p(_ptr(dl_ddelta)), C.c_void_p(_stream_ptr(stream))))
+
+
 def bsp_last_sums(handle) -> int:
     p = C.c_void_p()
     check(_lib.load().bsp_last_sums(handle, C.byref(p)))
@@ -170,6 +180,25 @@ class Plan:
         bsp_estimate_host(self.handle, spec_host, b, g, stream)
         return b, g
 
+    def spectrum(self, delta_x: torch.Tensor, stream=None) -> torch.Tensor:
+        """Half spectrum of a real FP32 field on the modes the plan uses (other entries zero)."""
+        if not delta_x.is_cuda or delta_x.dtype != torch.float32 or not delta_x.is_contiguous() \
+                or tuple(delta_x.shape) != (self.ng,) * 3:
+            raise ValueError(f"delta_x must be a contiguous CUDA float32 tensor of shape {(self.ng,) * 3}")
+        spec = torch.zeros(self.spec_shape(), dtype=torch.complex64, device=delta_x.device)
+        bsp_spectrum(self.handle, delta_x, spec, stream)
+        return spec
+
+    def grad(self, spec: torch.Tensor, dl_db: torch.Tensor, stream=None) -> torch.Tensor:
+        """dL/d delta(x) on the Ng^3 grid for dl_db = dL/dB per kept bin (float32 CUDA tensor)."""
+        self._check_spec(spec)
+        g = dl_db.to(device=spec.device, dtype=torch.float64).contiguous()
+        if g.numel() != self.n_triplets:
+            raise ValueError("dl_db must have one entry per kept bin")
+        out = torch.empty((self.ng,) * 3, dtype=torch.float32, device=spec.device)
+        bsp_grad(self.handle, spec, g, out, stream)
+        return out
+
     def check(self, stream=None):
         """Raise if a bounded device-side wait gave up in an earlier call (synchronises)."""
         bsp_plan_check(self.handle, stream)
@@ -192,4 +221,4 @@ class Plan:
 
 __all__ = ["Plan", "BispecError", "bsp_plan_create", "bsp_plan_destroy", "bsp_plan_info",
            "bsp_plan_triplets", "bsp_plan_grid", "bsp_shell_fields", "bsp_contract", "bsp_estimate",
-           "bsp_estimate_host", "bsp_last_sums", "bsp_plan_check", "bsp_version", "TRIPLET_DTYPE"]
+           "bsp_estimate_host", "bsp_spectrum", "bsp_grad", "bsp_last_sums", "bsp_plan_check", "bsp_version", "TRIPLET_DTYPE"]

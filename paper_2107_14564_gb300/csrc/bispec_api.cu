@@ -118,6 +118,22 @@ struct bsp_plan {
   int* d_tc_map = nullptr;
   double* tc_partial = nullptr;
   int* d_error = nullptr;
+  // gradient resources (built by the first bsp_grad call)
+  bool grad_ready = false;
+  bool ball_ready = false;
+  int adj_np = 0, adj_npairs = 0, adj_entries = 0;
+  int2* d_adj_pairs = nullptr;
+  int* d_w_ptr = nullptr;
+  int* d_w_idx = nullptr;
+  double* d_cnorm = nullptr;
+  float* d_w = nullptr;
+  float* d_gfields = nullptr;      // G_n on the evaluation grid
+  void* d_grad_spec = nullptr;     // gradient half spectrum of the ng grid (complex64)
+  void* d_tw_ng = nullptr;         // twiddles of the ng grid
+  ShellGeom* d_ball = nullptr;     // one pseudo-shell covering every shell's modes
+  Item *d_bxi = nullptr, *d_byi = nullptr;
+  int nbxi = 0, nbyi = 0;
+  void *g1b = nullptr, *g2b = nullptr;
   // per-stage timing (bsp_timing_enable)
   bool timing_on = false;
   int timing_max = 0;
@@ -181,12 +197,13 @@ int fft_lines_for(int len, int prec) {
   return l < 1 ? 1 : l;
 }
 
-void make_items(const bsp_plan* p, int lines_xy, int lines_z, std::vector<Item>& xi,
-                std::vector<Item>& yi, std::vector<Item>& zi) {
-  const int ng = p->ngs;
+// Work items of the three passes for shells `geom` on a grid of side `grid`.
+void make_items_g(const std::vector<ShellGeom>& geom, int grid, int lines_xy, int lines_z,
+                  std::vector<Item>& xi, std::vector<Item>& yi, std::vector<Item>& zi) {
+  const int ng = grid;
   xi.clear(); yi.clear(); zi.clear();
-  for (int n = 0; n < p->ns; ++n) {
-    const ShellGeom& g = p->geom[n];
+  for (int n = 0; n < (int)geom.size(); ++n) {
+    const ShellGeom& g = geom[n];
     const int r = g.r;
     for (int ky = -(r - 1); ky <= r - 1; ++ky) {
       const long long rem = (long long)g.qhi - 1 - (long long)ky * ky;
@@ -199,6 +216,11 @@ void make_items(const bsp_plan* p, int lines_xy, int lines_z, std::vector<Item>&
     for (int x = 0; x < ng; ++x)
       for (int y0 = 0; y0 < ng; y0 += lines_z) zi.push_back({n, x, y0, std::min(lines_z, ng - y0)});
   }
+}
+
+void make_items(const bsp_plan* p, int lines_xy, int lines_z, std::vector<Item>& xi,
+                std::vector<Item>& yi, std::vector<Item>& zi) {
+  make_items_g(p->geom, p->ngs, lines_xy, lines_z, xi, yi, zi);
 }
 
 // Tiles of up to 4 consecutive pairs x 4 consecutive c over a list of bins sorted by (a, b, c).
@@ -619,6 +641,91 @@ void stage_work(const bsp_plan* p, double* bytes, double* flops) {
   bytes[BSP_STAGE_FINALIZE] = 8.0 * (double)p->trips.size() * 3 + 8.0 * p->n_cells();
 }
 
+
+// Resources of the ng-grid transforms over the union of the shells (the ball of every shell
+// mode): twiddles, one pseudo-shell geometry, work items, pass buffers.
+bsp_status ball_setup(bsp_plan* p, cudaStream_t s) {
+  if (p->ball_ready) return BSP_OK;
+  bsp_status st;
+  if ((st = dev_alloc(p, (size_t)p->ng * sizeof(float2), &p->d_tw_ng)) != BSP_OK) return st;
+  if ((st = launch_twiddles<float>(p->d_tw_ng, p->ng, s)) != BSP_OK) return st;
+  // the final inverse transform covers the union of the shells as one pseudo-shell
+  std::vector<ShellGeom> ball(1);
+  ball[0].qlo = (int)p->q[0];
+  ball[0].qhi = (int)p->q[p->ns];
+  ball[0].r = (int)isqrt_ll(p->q[p->ns] - 1) + 1;
+  ball[0].pad = 0;
+  ball[0].g1_off = 0;
+  ball[0].g2_off = 0;
+  std::vector<Item> bx, by, bz;
+  make_items_g(ball, p->ng, warp_fft_lines(), 1, bx, by, bz);
+  p->nbxi = (int)bx.size();
+  p->nbyi = (int)by.size();
+  if ((st = dev_upload(p, ball, &p->d_ball, s)) != BSP_OK) return st;
+  if ((st = dev_upload(p, bx, &p->d_bxi, s)) != BSP_OK) return st;
+  if ((st = dev_upload(p, by, &p->d_byi, s)) != BSP_OK) return st;
+  const long long r = ball[0].r;
+  if ((st = dev_alloc(p, (size_t)p->ng * (2 * r - 1) * r * sizeof(float2), &p->g1b)) != BSP_OK) return st;
+  if ((st = dev_alloc(p, (size_t)p->ng * p->ng * r * sizeof(float2), &p->g2b)) != BSP_OK) return st;
+  p->ball_ready = true;
+  return BSP_OK;
+}
+
+// Resources of the gradient: adjoint pair table, W entries, buffers (first bsp_grad call).
+bsp_status grad_setup(bsp_plan* p, cudaStream_t s) {
+  if (p->grad_ready) return BSP_OK;
+  const int ns = p->ns;
+  p->adj_np = ns <= 32 ? 32 : 64;
+  const int np = p->adj_np;
+  // every unordered pair (x >= y) that is the complement of a bin position
+  std::vector<int> pid((size_t)ns * ns, -1);
+  std::vector<int2> pairs;
+  auto pair_index = [&](int x, int y) {
+    if (x < y) std::swap(x, y);
+    int& e = pid[(size_t)x * ns + y];
+    if (e < 0) { e = (int)pairs.size(); pairs.push_back(make_int2(x, y)); }
+    return e;
+  };
+  std::vector<std::vector<int>> lists;
+  auto add = [&](int pr, int n, int t) {
+    const size_t e = (size_t)pr * np + n;
+    if (lists.size() <= e) lists.resize(e + 1);
+    lists[e].push_back(t);
+  };
+  for (size_t t = 0; t < p->trips.size(); ++t) {
+    const bsp_triplet& b = p->trips[t];
+    add(pair_index(b.b, b.c), b.a, (int)t);
+    add(pair_index(b.a, b.c), b.b, (int)t);
+    add(pair_index(b.a, b.b), b.c, (int)t);
+  }
+  p->adj_npairs = (int)pairs.size();
+  p->adj_entries = p->adj_npairs * np;
+  lists.resize(p->adj_entries);
+  std::vector<int> ptr(p->adj_entries + 1, 0), idx;
+  for (int e = 0; e < p->adj_entries; ++e) {
+    ptr[e + 1] = ptr[e] + (int)lists[e].size();
+    idx.insert(idx.end(), lists[e].begin(), lists[e].end());
+  }
+  const double vc = pow(p->box_len / p->ng, 3.0);
+  const double norm = vc * vc * vc / (p->box_len * p->box_len * p->box_len);
+  std::vector<double> cnorm(p->trips.size());
+  for (size_t t = 0; t < p->trips.size(); ++t) cnorm[t] = norm / p->trips[t].tsum;
+  bsp_status st;
+  void* tmp = nullptr;
+  if ((st = dev_upload(p, pairs, &p->d_adj_pairs, s)) != BSP_OK) return st;
+  if ((st = dev_upload(p, ptr, &p->d_w_ptr, s)) != BSP_OK) return st;
+  if ((st = dev_upload(p, idx, &p->d_w_idx, s)) != BSP_OK) return st;
+  if ((st = dev_upload(p, cnorm, &p->d_cnorm, s)) != BSP_OK) return st;
+  if ((st = dev_alloc(p, (size_t)p->adj_entries * sizeof(float), &tmp)) != BSP_OK) return st;
+  p->d_w = static_cast<float*>(tmp);
+  if ((st = dev_alloc(p, p->field_bytes(), &tmp)) != BSP_OK) return st;
+  p->d_gfields = static_cast<float*>(tmp);
+  if ((st = dev_alloc(p, (size_t)p->ng * p->ng * (p->ng / 2 + 1) * sizeof(float2), &p->d_grad_spec)) != BSP_OK)
+    return st;
+  if ((st = ball_setup(p, s)) != BSP_OK) return st;
+  p->grad_ready = true;
+  return BSP_OK;
+}
 }  // namespace
 
 extern "C" {
@@ -913,6 +1020,92 @@ bsp_status bsp_plan_stage_work(const bsp_plan* p, double* bytes, double* flops) 
   if (!p || !bytes || !flops) return fail(BSP_ERR_INVALID_ARG, "NULL argument");
   stage_work(p, bytes, flops);
   return BSP_OK;
+}
+
+bsp_status bsp_spectrum(bsp_plan* p, const float* delta_x, void* spec_out, void* stream) {
+  if (!p || !delta_x || !spec_out) return fail(BSP_ERR_INVALID_ARG, "NULL argument");
+  if (p->prec == BSP_FP64) return fail(BSP_ERR_NOT_SUPPORTED, "bsp_spectrum needs an FP32 or mixed plan");
+  if (!warp_fft_supported(p->ng)) return fail(BSP_ERR_NOT_SUPPORTED, "bsp_spectrum needs ng = 2^p or 3 * 2^p in [128, 1024]");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  bsp_status st = ball_setup(p, s);
+  if (st != BSP_OK) return st;
+  PassArgs b{};
+  b.g1 = p->g1b;
+  b.g2 = p->g2b;
+  b.fields = spec_out;
+  b.tw = p->d_tw_ng;
+  b.geom = p->d_ball;
+  b.ng = p->ng;
+  b.ngs = p->ng;
+  b.rsd = 0;
+  b.beta = 0.0;
+  b.rmax = (int)isqrt_ll(p->q[p->ns] - 1) + 1;
+  st = launch_warp_zfpass(b, delta_x, (long long)p->ng * p->ng, p->n_sm, s);
+  if (st != BSP_OK) return st;
+  b.items = p->d_byi;
+  st = launch_warp_yfpass(b, p->nbyi, s);
+  if (st != BSP_OK) return st;
+  b.items = p->d_bxi;
+  return launch_warp_xfpass(b, p->nbxi, 1.f, s);
+}
+
+bsp_status bsp_grad(bsp_plan* p, const void* spec, const double* dl_db, float* dl_ddelta, void* stream) {
+  if (!p || !spec || !dl_db || !dl_ddelta) return fail(BSP_ERR_INVALID_ARG, "NULL argument");
+  if (p->prec == BSP_FP64) return fail(BSP_ERR_NOT_SUPPORTED, "bsp_grad needs an FP32 or mixed plan");
+  if (!warp_fft_supported(p->ngs) || !warp_fft_supported(p->ng))
+    return fail(BSP_ERR_NOT_SUPPORTED, "bsp_grad needs grid sides 2^p or 3 * 2^p in [128, 1024]");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  bsp_status st = grad_setup(p, s);
+  if (st != BSP_OK) return st;
+  // shell fields on the evaluation grid (recomputed: nothing is kept from a forward call)
+  st = plan_passes<float>(p, spec, p->fields, s, nullptr);
+  if (st != BSP_OK) return st;
+  // W and the adjoint products G_n
+  st = launch_build_w(dl_db, p->d_cnorm, p->d_w_ptr, p->d_w_idx, p->adj_entries, p->d_w, s);
+  if (st != BSP_OK) return st;
+  st = launch_adjoint_products(static_cast<const float*>(p->fields), p->nvox(), p->ns, p->adj_np, p->d_adj_pairs,
+                               p->adj_npairs, p->d_w, p->d_gfields, p->n_sm, s);
+  if (st != BSP_OK) return st;
+  // forward transforms of G_n, kept on each shell's modes: conj(.) K (ng/S)^3 into the ng spectrum
+  PassArgs a{};
+  a.g1 = p->g1;
+  a.g2 = p->g2;
+  a.fields = p->d_grad_spec;
+  a.tw = p->tw;
+  a.geom = p->d_geom;
+  a.ng = p->ng;
+  a.ngs = p->ngs;
+  a.rsd = p->rsd;
+  a.beta = p->beta;
+  a.rmax = p->rmax;
+  st = launch_warp_zfpass(a, p->d_gfields, (long long)p->ns * p->ngs * p->ngs, p->n_sm, s);
+  if (st != BSP_OK) return st;
+  a.items = p->d_wyi;
+  st = launch_warp_yfpass(a, p->nwyi, s);
+  if (st != BSP_OK) return st;
+  a.items = p->d_wxi;
+  st = launch_warp_xfpass(a, p->nwxi, (float)p->sum_scale, s);
+  if (st != BSP_OK) return st;
+  // one pruned inverse transform of the whole ball on the ng grid
+  PassArgs b{};
+  b.spec = p->d_grad_spec;
+  b.g1 = p->g1b;
+  b.g2 = p->g2b;
+  b.fields = dl_ddelta;
+  b.tw = p->d_tw_ng;
+  b.geom = p->d_ball;
+  b.ng = p->ng;
+  b.ngs = p->ng;
+  b.rsd = 0;
+  b.beta = 0.0;
+  b.rmax = (int)isqrt_ll(p->q[p->ns] - 1) + 1;
+  b.items = p->d_bxi;
+  st = launch_warp_xpass(b, p->nbxi, s);
+  if (st != BSP_OK) return st;
+  b.items = p->d_byi;
+  st = launch_warp_ypass(b, p->nbyi, s);
+  if (st != BSP_OK) return st;
+  return launch_warp_zpass(b, (long long)p->ng * p->ng, p->n_sm, s);
 }
 
 bsp_status bsp_last_sums(const bsp_plan* p, const double** msum) {

@@ -262,6 +262,173 @@ __global__ void __launch_bounds__(kZThreads) z_warp_kernel(PassArgs a, long long
   }
 }
 
+// ---------------------------------------------------------------- forward (adjoint) passes
+// The transposes of the passes above, for the gradient: a real field G_n on the S grid is taken
+// to sum_x G_n(x) e^{+i k.x} on the modes of shell n only, by the same unnormalised e^{+i}
+// transforms applied in the opposite order with pruned outputs:
+//   ZF: lines (n, x, y) along z, real input, keep k_z < r      -> H1[x][y][k_z]   (G2 layout)
+//   YF: lines (n, x, k_z) along y, keep |k_y| < r              -> H2[x][k_y][k_z] (G1 layout)
+//   XF: lines (n, k_y, k_z) along x, keep the shell's modes    -> conj(.) K(k) scale into the
+//       half spectrum of the ng grid (Eq. (3.4) factor K when the plan has RSD).
+template <int S>
+__global__ void __launch_bounds__(kZThreads) zf_warp_kernel(PassArgs a, const float* gfield, long long n_lines) {
+  constexpr int LPL = Radices<S>::lpl;
+  constexpr int LPW = 32 / LPL;
+  constexpr int E = S / LPL;
+  constexpr int kBufLd = S + S / 8;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* tw = reinterpret_cast<float2*>(smem_raw);
+  float2* bufs = tw + S;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < S; i += kZThreads) tw[i] = static_cast<const float2*>(a.tw)[i];
+  __syncthreads();
+  const int warp = tid >> 5;
+  const int sub = (tid & 31) / LPL;
+  const int lane = tid & (LPL - 1);
+  float2* buf = bufs + (size_t)(warp * LPW + sub) * kBufLd;
+  const long long plane = (long long)S * S;
+  const long long stride = (long long)gridDim.x * (kZThreads / 32) * LPW;
+  constexpr int R1 = first_radix<S>();
+  constexpr int BPL = S / (R1 * LPL);
+  constexpr int RL = last_radix<S>();
+  constexpr int BPLL = S / (RL * LPL);
+  for (long long line = ((long long)blockIdx.x * (kZThreads / 32) + warp) * LPW + sub; line < n_lines;
+       line += stride) {
+    const int n = (int)(line / plane);
+    const long long xy = line - (long long)n * plane;
+    const ShellGeom g = a.geom[n];
+    const int r = g.r;
+    const float* src = gfield + (long long)n * S * plane + xy * S;
+    float2 v[E];
+#pragma unroll
+    for (int b = 0; b < BPL; ++b)
+#pragma unroll
+      for (int rr = 0; rr < R1; ++rr) v[b * R1 + rr] = make_float2(src[lane + b * LPL + rr * (S / R1)], 0.f);
+    warp_fft_from<S, LPL, 0, 1, 1>(v, buf, lane, tw);
+    float2* dst = static_cast<float2*>(a.g2) + g.g2_off + xy * r;
+#pragma unroll
+    for (int b = 0; b < BPLL; ++b)
+#pragma unroll
+      for (int rr = 0; rr < RL; ++rr) {
+        const int k = lane + b * LPL + rr * (S / RL);
+        if (k < r) dst[k] = v[b * RL + rr];
+      }
+  }
+}
+
+// XPASS = false: YF (input H1 = G2 layout, output H2 = G1 layout).
+// XPASS = true : XF (input H2, output the ng half spectrum `a.fields` reinterpreted as complex).
+template <int N, bool XPASS>
+__global__ void __launch_bounds__(XY<N>::kThreads) xyf_warp_kernel(PassArgs a, float scale) {
+  constexpr int LPL = XY<N>::kLpl;
+  constexpr int NT = XY<N>::kThreads;
+  constexpr int E = N / LPL;
+  constexpr int kBufLd = N + N / 8;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* tw = reinterpret_cast<float2*>(smem_raw);  // N
+  float2* bufs = tw + N;                               // kLines x kBufLd
+  float2* tile = bufs + (size_t)kLines * kBufLd;       // N x kTileLd input, then (2r-1) x kTileLd output
+  const Item it = a.items[blockIdx.x];
+  const ShellGeom g = a.geom[it.n];
+  const int r = g.r;
+  const int w = 2 * r - 1;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < N; i += NT) tw[i] = static_cast<const float2*>(a.tw)[i];
+  // ---- input tile [position along the line][line], contiguous along k_z in memory
+  const float2* src;
+  long long row_stride;
+  if (XPASS) {
+    src = static_cast<const float2*>(a.g1) + g.g1_off + (long long)(it.u + r - 1) * r + it.v0;
+    row_stride = (long long)w * r;
+  } else {
+    src = static_cast<const float2*>(a.g2) + g.g2_off + (long long)it.u * N * r + it.v0;
+    row_stride = r;
+  }
+  for (int idx = tid; idx < N * kLines; idx += NT) {
+    const int l = idx & (kLines - 1);
+    const int y = idx >> 4;
+    tile[y * kTileLd + l] = l < it.cnt ? src[y * row_stride + l] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  {
+    constexpr int R1 = first_radix<N>();
+    constexpr int BPL = N / (R1 * LPL);
+    const int l = tid / LPL;
+    const int lane = tid & (LPL - 1);
+    float2 v[E];
+#pragma unroll
+    for (int b = 0; b < BPL; ++b)
+#pragma unroll
+      for (int rr = 0; rr < R1; ++rr) v[b * R1 + rr] = tile[(lane + b * LPL + rr * (N / R1)) * kTileLd + l];
+    float2* buf = bufs + (size_t)l * kBufLd;
+    warp_fft_from<N, LPL, 0, 1, 1>(v, buf, lane, tw);
+    constexpr int RL = last_radix<N>();
+    constexpr int BPLL = N / (RL * LPL);
+    __syncwarp();
+#pragma unroll
+    for (int b = 0; b < BPLL; ++b)
+#pragma unroll
+      for (int rr = 0; rr < RL; ++rr) buf[padi(lane + b * LPL + rr * (N / RL))] = v[b * RL + rr];
+  }
+  __syncthreads();
+  // ---- keep the positions |k| <= r - 1: row = k + r - 1
+  if (XPASS) {
+    float2* spec = reinterpret_cast<float2*>(a.fields);
+    const int ng = a.ng;
+    const int hz = ng / 2 + 1;
+    const int ky = it.u;
+    const int iy = ky < 0 ? ky + ng : ky;
+    for (int idx = tid; idx < w * kLines; idx += NT) {
+      const int l = idx & (kLines - 1);
+      const int row = idx >> 4;
+      const int kx = row - (r - 1);
+      const int kz = it.v0 + l;
+      const int q = kx * kx + ky * ky + kz * kz;
+      if (l < it.cnt && q >= g.qlo && q < g.qhi) {
+        float2 val = bufs[(size_t)l * kBufLd + padi(kx < 0 ? kx + N : kx)];
+        float fac = scale;
+        if (a.rsd) fac *= (float)(1.0 + a.beta * (double)(kz * kz) / (double)q);
+        const int ix = kx < 0 ? kx + ng : kx;
+        spec[((long long)ix * ng + iy) * hz + kz] = make_float2(val.x * fac, -val.y * fac);
+      }
+    }
+  } else {
+    float2* dst = static_cast<float2*>(a.g1) + g.g1_off + (long long)it.u * w * r + it.v0;
+    for (int idx = tid; idx < w * kLines; idx += NT) {
+      const int l = idx & (kLines - 1);
+      const int row = idx >> 4;
+      const int ky = row - (r - 1);
+      if (l < it.cnt) dst[(long long)row * r + l] = bufs[(size_t)l * kBufLd + padi(ky < 0 ? ky + N : ky)];
+    }
+  }
+}
+
+template <int N, bool XPASS>
+bsp_status launch_xyf(const PassArgs& a, int n_items, float scale, cudaStream_t s) {
+  if (n_items == 0) return BSP_OK;
+  const size_t smem = ((size_t)N + (size_t)kLines * (N + N / 8) + (size_t)N * kTileLd) * sizeof(float2);
+  BSP_CUDA(cudaFuncSetAttribute(xyf_warp_kernel<N, XPASS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  xyf_warp_kernel<N, XPASS><<<n_items, XY<N>::kThreads, smem, s>>>(a, scale);
+  BSP_CUDA(cudaGetLastError());
+  return BSP_OK;
+}
+
+template <int S>
+bsp_status launch_zf(const PassArgs& a, const float* gfield, long long n_lines, int n_sm, cudaStream_t s) {
+  constexpr int LPW = 32 / Radices<S>::lpl;
+  const size_t smem = ((size_t)S + (size_t)(kZThreads / 32) * LPW * (S + S / 8)) * sizeof(float2);
+  BSP_CUDA(cudaFuncSetAttribute(zf_warp_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  BSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, zf_warp_kernel<S>, kZThreads, smem));
+  long long blocks = (long long)std::max(per_sm, 1) * n_sm;
+  const long long need = (n_lines + (kZThreads / 32) * LPW - 1) / ((kZThreads / 32) * LPW);
+  if (blocks > need) blocks = need;
+  if (blocks < 1) blocks = 1;
+  zf_warp_kernel<S><<<(unsigned)blocks, kZThreads, smem, s>>>(a, gfield, n_lines);
+  BSP_CUDA(cudaGetLastError());
+  return BSP_OK;
+}
+
 template <int N, bool XPASS>
 bsp_status launch_xy(const PassArgs& a, int n_items, cudaStream_t s) {
   if (n_items == 0) return BSP_OK;
@@ -321,6 +488,33 @@ bsp_status launch_warp_ypass(const PassArgs& a, int n_items, cudaStream_t s) {
 bsp_status launch_warp_zpass(const PassArgs& a, long long n_lines, int n_sm, cudaStream_t s) {
   switch (a.ngs) {
 #define X(S) case S: return launch_z<S>(a, n_lines, n_sm, s);
+    BSP_WARP_SIZES(X)
+#undef X
+  }
+  return fail_c(BSP_ERR_NOT_SUPPORTED, "warp FFT: unsupported grid");
+}
+
+bsp_status launch_warp_zfpass(const PassArgs& a, const float* gfield, long long n_lines, int n_sm, cudaStream_t s) {
+  switch (a.ngs) {
+#define X(S) case S: return launch_zf<S>(a, gfield, n_lines, n_sm, s);
+    BSP_WARP_SIZES(X)
+#undef X
+  }
+  return fail_c(BSP_ERR_NOT_SUPPORTED, "warp FFT: unsupported grid");
+}
+
+bsp_status launch_warp_yfpass(const PassArgs& a, int n_items, cudaStream_t s) {
+  switch (a.ngs) {
+#define X(S) case S: return launch_xyf<S, false>(a, n_items, 1.f, s);
+    BSP_WARP_SIZES(X)
+#undef X
+  }
+  return fail_c(BSP_ERR_NOT_SUPPORTED, "warp FFT: unsupported grid");
+}
+
+bsp_status launch_warp_xfpass(const PassArgs& a, int n_items, float scale, cudaStream_t s) {
+  switch (a.ngs) {
+#define X(S) case S: return launch_xyf<S, true>(a, n_items, scale, s);
     BSP_WARP_SIZES(X)
 #undef X
   }

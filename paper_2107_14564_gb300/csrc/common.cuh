@@ -81,6 +81,11 @@ int warp_fft_lines();
 bsp_status launch_warp_xpass(const PassArgs& a, int n_items, cudaStream_t s);
 bsp_status launch_warp_ypass(const PassArgs& a, int n_items, cudaStream_t s);
 bsp_status launch_warp_zpass(const PassArgs& a, long long n_lines, int n_sm, cudaStream_t s);
+// Forward (adjoint) passes: real fields gfield [n][S^3] -> per-shell modes, written as
+// conj(sum_x G e^{+ik.x}) * K * scale into the ng half spectrum a.fields (complex64).
+bsp_status launch_warp_zfpass(const PassArgs& a, const float* gfield, long long n_lines, int n_sm, cudaStream_t s);
+bsp_status launch_warp_yfpass(const PassArgs& a, int n_items, cudaStream_t s);
+bsp_status launch_warp_xfpass(const PassArgs& a, int n_items, float scale, cudaStream_t s);
 
 // ---------------------------------------------------------------- contraction tables
 // A tile covers up to 4 consecutive pairs and 4 consecutive c shells; map[16] gives the kept
@@ -161,5 +166,11 @@ bsp_status launch_contract_tc(const TcArgs& a, cudaStream_t s);
 // msum[t] = scale * sum_y partial[y][map[t]], map[t] = (mtile * 128 + row) * np + c of bin t
 bsp_status launch_reduce_tc(const TcArgs& a, const int* map, int n_out, double* msum, double scale,
                             cudaStream_t s);
+
+// ---------------------------------------------------------------- gradient (bispec_grad.cu)
+bsp_status launch_build_w(const double* g, const double* cnorm, const int* ptr, const int* idx, int n_entries,
+                          float* W, cudaStream_t s);
+bsp_status launch_adjoint_products(const float* fields, long long nvox, int ns, int np, const int2* pairs,
+                                   int npairs, const float* W, float* G, int n_sm, cudaStream_t s);
 
 }  // namespace bsp

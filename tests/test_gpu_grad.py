@@ -1,0 +1,99 @@
+"""The forward spectrum, the adjoint (bsp_grad) and the autograd Function against the FP64
+oracle's adjoint (itself pinned by finite differences). Needs a GB300."""
+import numpy as np
+import pytest
+
+import fieldgen
+from oracle import fbe
+from oracle import grad as G
+from oracle import plan as P
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2107_14564_gb300 import binding
+    return binding
+
+
+def _setup(lib, ng, ns, top, seed, beta=None, prec="fp32"):
+    edges = P.linear_edges(ns, 1.0, top)
+    delta = fieldgen.quadratic_field(ng, float(ng), 1.5, 0.2, seed).astype(np.float32)
+    gp = lib.Plan(ng, float(ng), edges, rsd=beta is not None, beta=beta or 0.0, precision=prec)
+    pl = P.make_plan(ng, float(ng), edges)
+    return edges, delta, gp, pl
+
+
+def test_spectrum_on_shell_modes(lib):
+    ng = 128
+    _, delta, gp, pl = _setup(lib, ng, 8, 32.0, 3)
+    spec = gp.spectrum(torch.from_numpy(delta).cuda()).cpu().numpy()
+    want = np.fft.rfftn(delta.astype(np.float64))
+    sidx = P.shell_index_half(pl)
+    sel = sidx >= 0
+    err = np.abs(spec[sel] - want[sel]).max() / np.abs(want[sel]).max()
+    assert err < 1e-5
+    assert np.all(spec[~sel] == 0)
+
+
+@pytest.mark.parametrize("beta,prec", [(None, "fp32"), (0.5, "fp32"), (None, "mixed_bf16x3")])
+def test_adjoint_matches_oracle(lib, beta, prec):
+    ng = 128
+    _, delta, gp, pl = _setup(lib, ng, 8, 32.0, 5, beta, prec)
+    trips = [tuple(int(v) for v in t) for t in zip(gp.triplets["a"], gp.triplets["b"], gp.triplets["c"])]
+    tsum = gp.triplets["tsum"]
+    g = fieldgen.random_weights(len(trips), 9)
+    want = G.vjp(delta.astype(np.float64), pl, trips, tsum, g, beta=beta)
+    d = torch.from_numpy(delta).cuda()
+    spec = gp.spectrum(d)
+    got = gp.grad(spec, torch.from_numpy(g).cuda()).cpu().numpy()
+    gp.check()
+    err = np.abs(got - want).max() / np.abs(want).max()
+    assert err < 1e-4, err
+
+
+def test_autograd_function_loss(lib):
+    """loss = sum (B - B_ana)^2 / B_ana^2 over the bins; d loss / d delta via backward() against the
+    oracle adjoint driven by the same dL/dB."""
+    from oracle import analytic as A
+    from paper_2107_14564_gb300.autograd import bispectrum
+    ng = 128
+    _, delta, gp, pl = _setup(lib, ng, 8, 32.0, 7)
+    tr = gp.triplets
+    kf = pl.kf
+    p = [A.power_law(kf * tr[k], 1.5) for k in ("k1", "k2", "k3")]
+    bana = torch.from_numpy(A.b_ana(p[0], p[1], p[2], 0.2)).cuda()
+    d = torch.from_numpy(delta).cuda().requires_grad_(True)
+    b = bispectrum(d, gp)
+    loss = (((b - bana) / bana) ** 2).sum()
+    loss.backward()
+    g = (2.0 * (b.detach() - bana) / bana ** 2).cpu().numpy()
+    trips = [tuple(int(v) for v in t) for t in zip(tr["a"], tr["b"], tr["c"])]
+    want = G.vjp(delta.astype(np.float64), pl, trips, tr["tsum"], g)
+    got = d.grad.cpu().numpy()
+    assert np.abs(got - want).max() / np.abs(want).max() < 1e-4
+    # and the forward equals the oracle estimate of the same field
+    res = fbe.estimate(np.fft.rfftn(delta.astype(np.float64)), pl, with_abs=True)
+    assert np.max(np.abs(b.detach().cpu().numpy() - res["b"]) / res["b_scale"]) < 1e-4
+
+
+@pytest.mark.slow
+def test_adjoint_config5_sampled_voxels(lib):
+    """Ng=256, 24 shells up to k_Nyq/2, FP32: the adjoint at 64 seeded voxels against the oracle."""
+    ng = 256
+    _, delta, gp, pl = _setup(lib, ng, 24, 64.0, 5)
+    tr = gp.triplets
+    trips = [tuple(int(v) for v in t) for t in zip(tr["a"], tr["b"], tr["c"])]
+    g = fieldgen.random_weights(len(trips), 6)
+    want = G.vjp(delta.astype(np.float64), pl, trips, tr["tsum"], g)
+    spec = gp.spectrum(torch.from_numpy(delta).cuda())
+    got = gp.grad(spec, torch.from_numpy(g).cuda()).cpu().numpy()
+    vox = fieldgen.random_voxels(ng, 64, 6)
+    scale = np.abs(want).max()
+    assert np.abs(got.ravel()[vox] - want.ravel()[vox]).max() / scale < 1e-4
+    assert np.abs(got - want).max() / scale < 1e-4
