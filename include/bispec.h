@@ -164,6 +164,29 @@ BSP_API bsp_status bsp_spectrum(bsp_plan* plan, const float* delta_x, void* spec
 BSP_API bsp_status bsp_grad(bsp_plan* plan, const void* spec, const double* dl_db, float* dl_ddelta,
                             void* stream);
 
+/* Many estimates in one call: bsp_estimate(plans[i], specs[i], b_triplet[i], b_grid[i]) for i < n,
+ * enqueued in order on `stream` (b_grid may be NULL, or hold NULL entries). Plans may repeat and
+ * may differ in grid size; estimates that share a plan run one after the other (they share its
+ * buffers). Errors: those of bsp_estimate, for the first failing entry. */
+BSP_API bsp_status bsp_estimate_batched(bsp_plan* const* plans, const void* const* specs, int n,
+                                        double* const* b_triplet, double* const* b_grid, void* stream);
+
+typedef struct bsp_batch bsp_batch;
+
+/* Capture the same n estimates as one CUDA graph for repeated replay with bsp_batch_run: every
+ * pointer passed here is baked into the graph and must stay valid (and keep its size) for the
+ * batch's lifetime; each distinct plan first runs one estimate outside the capture (on `stream`,
+ * synchronised). Plans must not have timing enabled. Errors: BSP_ERR_INVALID_ARG, BSP_ERR_CUDA. */
+BSP_API bsp_status bsp_batch_create(bsp_plan* const* plans, const void* const* specs, int n,
+                                    double* const* b_triplet, double* const* b_grid, void* stream,
+                                    bsp_batch** out);
+
+/* Replay a captured batch on `stream` (one graph launch for every kernel of every estimate). */
+BSP_API bsp_status bsp_batch_run(bsp_batch* batch, void* stream);
+
+/* Free a batch (not its plans or buffers). NULL is a no-op. */
+BSP_API bsp_status bsp_batch_destroy(bsp_batch* batch);
+
 /* Per-bin numerators of the last bsp_estimate on this plan, msum[t] = sum_x d_a d_b d_c, as a
  * device pointer owned by the plan (n_triplets doubles, valid until the next call on it). */
 BSP_API bsp_status bsp_last_sums(const bsp_plan* plan, const double** msum);

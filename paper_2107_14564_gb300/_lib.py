@@ -49,6 +49,13 @@ SIGNATURES = {
     "bsp_contract": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "bsp_estimate": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "bsp_estimate_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "bsp_estimate_batched": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int,
+                                       C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_void_p]),
+    "bsp_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int,
+                                   C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_void_p,
+                                   C.POINTER(C.c_void_p)]),
+    "bsp_batch_run": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "bsp_batch_destroy": (C.c_int, [C.c_void_p]),
     "bsp_spectrum": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "bsp_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "bsp_last_sums": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p)]),

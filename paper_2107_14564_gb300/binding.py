@@ -111,6 +111,56 @@ def bsp_version() -> str:
     return _lib.load().bsp_version().decode()
 
 
+def _ptr_array(items):
+    arr = (C.c_void_p * len(items))()
+    for i, x in enumerate(items):
+        arr[i] = None if x is None else (x.handle.value if isinstance(x, Plan) else _ptr(x))
+    return arr
+
+
+def bsp_estimate_batched(plans, specs, b_triplets, b_grids=None, stream=None) -> None:
+    n = len(plans)
+    grids = _ptr_array(b_grids) if b_grids is not None else None
+    check(_lib.load().bsp_estimate_batched(_ptr_array(plans), _ptr_array(specs), n, _ptr_array(b_triplets),
+                                           grids, C.c_void_p(_stream_ptr(stream))))
+
+
+class Batch:
+    """A captured CUDA graph of estimates over (plan, spectrum) pairs with preallocated outputs.
+    The spectra tensors must stay alive (and unchanged in place) while the batch is used."""
+
+    def __init__(self, plans, specs, stream=None, with_grid=False):
+        self.plans = list(plans)
+        self.specs = list(specs)
+        for p, sp in zip(self.plans, self.specs):
+            p._check_spec(sp)
+        dev = self.specs[0].device
+        self.b = [torch.empty(p.n_triplets, dtype=torch.float64, device=dev) for p in self.plans]
+        self.grid = [torch.empty((p.n_shells, p.n_mu, p.n_t), dtype=torch.float64, device=dev)
+                     for p in self.plans] if with_grid else None
+        out = C.c_void_p()
+        grids = _ptr_array(self.grid) if self.grid is not None else None
+        check(_lib.load().bsp_batch_create(_ptr_array(self.plans), _ptr_array(self.specs), len(self.plans),
+                                           _ptr_array(self.b), grids, C.c_void_p(_stream_ptr(stream)),
+                                           C.byref(out)))
+        self.handle = out
+
+    def run(self, stream=None):
+        check(_lib.load().bsp_batch_run(self.handle, C.c_void_p(_stream_ptr(stream))))
+        return self.b
+
+    def close(self):
+        if self.handle is not None:
+            check(_lib.load().bsp_batch_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 # ------------------------------------------------------------------ convenience object
 class Plan:
     """A binning plan plus its output tensors on the current CUDA device.
@@ -221,4 +271,4 @@ class Plan:
 
 __all__ = ["Plan", "BispecError", "bsp_plan_create", "bsp_plan_destroy", "bsp_plan_info",
            "bsp_plan_triplets", "bsp_plan_grid", "bsp_shell_fields", "bsp_contract", "bsp_estimate",
-           "bsp_estimate_host", "bsp_spectrum", "bsp_grad", "bsp_last_sums", "bsp_plan_check", "bsp_version", "TRIPLET_DTYPE"]
+           "bsp_estimate_host", "bsp_estimate_batched", "Batch", "bsp_spectrum", "bsp_grad", "bsp_last_sums", "bsp_plan_check", "bsp_version", "TRIPLET_DTYPE"]

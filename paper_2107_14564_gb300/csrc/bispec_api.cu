@@ -152,6 +152,12 @@ struct bsp_plan {
   size_t field_bytes() const { return (size_t)ns * (size_t)nvox() * elem(); }
 };
 
+struct bsp_batch {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int n = 0;
+};
+
 namespace {
 
 bsp_status dev_alloc(bsp_plan* p, size_t bytes, void** out) {
@@ -950,6 +956,73 @@ bsp_status bsp_estimate(bsp_plan* p, const void* spec, double* b_triplet, double
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (p->prec == BSP_FP64) return estimate_impl<double>(p, spec, b_triplet, b_grid, s);
   return estimate_impl<float>(p, spec, b_triplet, b_grid, s);
+}
+
+bsp_status bsp_estimate_batched(bsp_plan* const* plans, const void* const* specs, int n, double* const* b_triplet,
+                                double* const* b_grid, void* stream) {
+  if (n < 0 || (n > 0 && (!plans || !specs || !b_triplet))) return fail(BSP_ERR_INVALID_ARG, "NULL argument");
+  for (int i = 0; i < n; ++i) {
+    bsp_status st = bsp_estimate(plans[i], specs[i], b_triplet[i], b_grid ? b_grid[i] : nullptr, stream);
+    if (st != BSP_OK) return st;
+  }
+  return BSP_OK;
+}
+
+bsp_status bsp_batch_create(bsp_plan* const* plans, const void* const* specs, int n, double* const* b_triplet,
+                            double* const* b_grid, void* stream, bsp_batch** out) {
+  if (!out) return fail(BSP_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (n < 1 || !plans || !specs || !b_triplet) return fail(BSP_ERR_INVALID_ARG, "NULL argument or n < 1");
+  for (int i = 0; i < n; ++i) {
+    if (!plans[i] || !specs[i] || !b_triplet[i]) return fail(BSP_ERR_INVALID_ARG, "NULL entry");
+    if (plans[i]->timing_on) return fail(BSP_ERR_INVALID_ARG, "disable plan timing before capturing a batch");
+  }
+  // warm every distinct plan once outside capture (kernel attributes, lazy module loading)
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  for (int i = 0; i < n; ++i) {
+    bool seen = false;
+    for (int j = 0; j < i; ++j) seen = seen || plans[j] == plans[i];
+    if (seen) continue;
+    bsp_status st = bsp_estimate(plans[i], specs[i], b_triplet[i], b_grid ? b_grid[i] : nullptr, stream);
+    if (st != BSP_OK) return st;
+  }
+  BSP_CUDA(cudaStreamSynchronize(s));
+  cudaStream_t cap;
+  BSP_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) { cudaStreamDestroy(cap); return cuda_fail(e, "cudaStreamBeginCapture"); }
+  bsp_status st = BSP_OK;
+  for (int i = 0; i < n && st == BSP_OK; ++i)
+    st = bsp_estimate(plans[i], specs[i], b_triplet[i], b_grid ? b_grid[i] : nullptr, cap);
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamEndCapture(cap, &graph);
+  cudaStreamDestroy(cap);
+  if (st != BSP_OK) { if (graph) cudaGraphDestroy(graph); return st; }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  if (e != cudaSuccess) { cudaGraphDestroy(graph); return cuda_fail(e, "cudaGraphInstantiate"); }
+  bsp_batch* b = new (std::nothrow) bsp_batch();
+  if (!b) { cudaGraphExecDestroy(exec); cudaGraphDestroy(graph); return fail(BSP_ERR_OOM, "host allocation failed"); }
+  b->graph = graph;
+  b->exec = exec;
+  b->n = n;
+  *out = b;
+  return BSP_OK;
+}
+
+bsp_status bsp_batch_run(bsp_batch* b, void* stream) {
+  if (!b) return fail(BSP_ERR_INVALID_ARG, "batch is NULL");
+  BSP_CUDA(cudaGraphLaunch(b->exec, static_cast<cudaStream_t>(stream)));
+  return BSP_OK;
+}
+
+bsp_status bsp_batch_destroy(bsp_batch* b) {
+  if (!b) return BSP_OK;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  delete b;
+  return BSP_OK;
 }
 
 bsp_status bsp_estimate_host(bsp_plan* p, const void* spec_host, double* b_triplet_host, double* b_grid_host,
