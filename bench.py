@@ -37,6 +37,13 @@ WORKLOADS = {
                   text="Ng=256 L=256 quadratic NG field P=k^-1.5 f=0.05, 24 linear shells "
                        "k_f..k_Nyq/2, 20x20 (mu,t) cells"),
 }
+WORKLOADS["prof384"] = dict(ng=384, box=384.0, n_index=1.5, f_ng=0.05, beta=None, ns=8, top=96.0,
+                            n_mu=10, n_t=10, seed=11,
+                            text="profiling case: Ng=384 L=384, 8 linear shells k_f..k_Nyq/2, 10x10 cells")
+WORKLOADS["batch64"] = dict(text="64 seeded quadratic NG fields (P=k^-1.5, f=0.05) on uneven grids: 16 x 128^3, "
+                                 "24 x 192^3, 24 x 256^3 (L=Ng), 16 linear shells k_f..k_Nyq/2 each, 10x10 "
+                                 "(mu,t) cells, one captured CUDA graph",
+                            grids=((128, 16), (192, 24), (256, 24)), ns=16, n_mu=10, n_t=10)
 DTYPES = {"fp64": "f64", "fp32": "f32", "mixed_bf16x3": "bf16x3/f32"}
 STAGES = ["xpass", "ypass", "zpass", "contract", "finalize"]
 STAGE_KERNEL_SRC = {"xpass": "bispec_fft_warp.cu", "ypass": "bispec_fft_warp.cu", "zpass": "bispec_fft_warp.cu",
@@ -382,6 +389,60 @@ def run_ours(args, w):
         dist.destroy_process_group()
 
 
+def run_batch(args, w):
+    """The batched workload: every field's estimate in one CUDA-graph replay per step."""
+    import numpy as np
+    import torch
+    import fieldgen
+    from paper_2107_14564_gb300 import binding
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    plans, specs, nbytes = [], [], 0
+    for ng, count in w["grids"]:
+        plan = binding.Plan(ng, float(ng), np.linspace(1.0, ng / 4, w["ns"] + 1), w["n_mu"], w["n_t"],
+                            precision=args.precision)
+        for i in range(count):
+            sp = fieldgen.half_spectrum_c64(fieldgen.quadratic_field(ng, float(ng), 1.5, 0.05, 100 + len(specs)))
+            nbytes += sp.nbytes
+            plans.append(plan)
+            specs.append(torch.from_numpy(sp).cuda())
+    bins = sum(p.n_triplets for p in plans)
+    batch = binding.Batch(plans, specs)
+    for _ in range(args.warmup):
+        batch.run()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        batch.run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    # the same estimates launched one by one (no graph) for comparison
+    e0.record(stream)
+    for p, sp in zip(plans, specs):
+        p.estimate(sp, with_grid=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_loop = e0.elapsed_time(e1)
+    line = {"metric": "triangle bins/sec over the 64-field batch", "value": bins / (ms / 1000.0),
+            "unit": "bins/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": DTYPES[args.precision], "data": "synthetic",
+            "config": {"workload": w["text"], "precision": args.precision, "fields": len(specs),
+                       "l2": "inputs larger than L2 (%.1f GB of spectra)" % (nbytes / 1e9)},
+            "n_bins": bins, "fields_per_sec": sum(p.n_shells for p in plans) / (ms / 1000.0),
+            "ms_without_graph": ms_loop, "gpu_launches": 6 * len(specs), "clocks": clk,
+            "roofline": None, "cpu_baseline": None, "e2e": None}
+    print(json.dumps(line), flush=True)
+    batch.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -400,6 +461,8 @@ def main():
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, w)
+    elif args.workload == "batch64":
+        run_batch(args, w)
     else:
         run_ours(args, w)
 

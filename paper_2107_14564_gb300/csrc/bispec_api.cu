@@ -108,6 +108,8 @@ struct bsp_plan {
   int* cell_idx = nullptr;
   // warp-per-line FP32 passes
   bool warp_fft = false;
+  float2 *d_stw = nullptr, *d_stw_half = nullptr;        // stage twiddles, lengths ngs and ngs/2
+  float2 *d_stw_ng = nullptr, *d_stw_ng_half = nullptr;  // the same for ng (ball transforms)
   Item *d_wxi = nullptr, *d_wyi = nullptr;
   int nwxi = 0, nwyi = 0;
   int rmax = 0;
@@ -551,6 +553,8 @@ bsp_status plan_passes(bsp_plan* p, const void* spec, void* fields, cudaStream_t
   a.rsd = p->rsd;
   a.beta = p->beta;
   a.rmax = p->rmax;
+  a.stw = p->d_stw;
+  a.stw_half = p->d_stw_half;
   bsp_status st;
   if (std::is_same<T, float>::value && p->warp_fft) {
     a.items = p->d_wxi;
@@ -655,6 +659,15 @@ bsp_status ball_setup(bsp_plan* p, cudaStream_t s) {
   bsp_status st;
   if ((st = dev_alloc(p, (size_t)p->ng * sizeof(float2), &p->d_tw_ng)) != BSP_OK) return st;
   if ((st = launch_twiddles<float>(p->d_tw_ng, p->ng, s)) != BSP_OK) return st;
+  {
+    std::vector<float2> t1, t2;
+    warp_stage_table(p->ng, t1);
+    warp_stage_table(p->ng / 2, t2);
+    if (t1.empty()) t1.assign(1, make_float2(0.f, 0.f));
+    if (t2.empty()) t2.assign(1, make_float2(0.f, 0.f));
+    if ((st = dev_upload(p, t1, &p->d_stw_ng, s)) != BSP_OK) return st;
+    if ((st = dev_upload(p, t2, &p->d_stw_ng_half, s)) != BSP_OK) return st;
+  }
   // the final inverse transform covers the union of the shells as one pseudo-shell
   std::vector<ShellGeom> ball(1);
   ball[0].qlo = (int)p->q[0];
@@ -835,6 +848,12 @@ bsp_status bsp_plan_create(const bsp_plan_desc* desc, void* stream, bsp_plan** o
   for (const ShellGeom& g : p->geom) p->rmax = std::max(p->rmax, g.r);
   p->warp_fft = p->prec != BSP_FP64 && warp_fft_supported(p->ngs);
   if (p->warp_fft) {
+    std::vector<float2> t1, t2;
+    warp_stage_table(p->ngs, t1);
+    warp_stage_table(p->ngs / 2, t2);
+    if (t2.empty()) t2.assign(1, make_float2(0.f, 0.f));
+    TRY(dev_upload(p, t1, &p->d_stw, s));
+    TRY(dev_upload(p, t2, &p->d_stw_half, s));
     std::vector<Item> wx, wy, wz;
     make_items(p, warp_fft_lines(), 1, wx, wy, wz);
     p->nwxi = (int)wx.size();
@@ -1113,6 +1132,8 @@ bsp_status bsp_spectrum(bsp_plan* p, const float* delta_x, void* spec_out, void*
   b.rsd = 0;
   b.beta = 0.0;
   b.rmax = (int)isqrt_ll(p->q[p->ns] - 1) + 1;
+  b.stw = p->d_stw_ng;
+  b.stw_half = p->d_stw_ng_half;
   st = launch_warp_zfpass(b, delta_x, (long long)p->ng * p->ng, p->n_sm, s);
   if (st != BSP_OK) return st;
   b.items = p->d_byi;
@@ -1151,6 +1172,8 @@ bsp_status bsp_grad(bsp_plan* p, const void* spec, const double* dl_db, float* d
   a.rsd = p->rsd;
   a.beta = p->beta;
   a.rmax = p->rmax;
+  a.stw = p->d_stw;
+  a.stw_half = p->d_stw_half;
   st = launch_warp_zfpass(a, p->d_gfields, (long long)p->ns * p->ngs * p->ngs, p->n_sm, s);
   if (st != BSP_OK) return st;
   a.items = p->d_wyi;
@@ -1172,6 +1195,8 @@ bsp_status bsp_grad(bsp_plan* p, const void* spec, const double* dl_db, float* d
   b.rsd = 0;
   b.beta = 0.0;
   b.rmax = (int)isqrt_ll(p->q[p->ns] - 1) + 1;
+  b.stw = p->d_stw_ng;
+  b.stw_half = p->d_stw_ng_half;
   b.items = p->d_bxi;
   st = launch_warp_xpass(b, p->nbxi, s);
   if (st != BSP_OK) return st;

@@ -16,14 +16,26 @@
 #include "common.cuh"
 #include "fft_radix.cuh"
 
+#include <math.h>
+
+#include <vector>
+
 namespace bsp {
 namespace {
 
-constexpr int kLines = 16;          // lines per X/Y block
+constexpr int kLines = 8;           // lines per X/Y block
 constexpr int kZThreads = 256;      // 8 warps, one line at a time each
 constexpr int kTileLd = kLines + 1; // padded tile row (complex)
 
-__device__ __forceinline__ int padi(int i) { return i + (i >> 3); }
+// Padding of the per-line exchange buffers: one spare slot every 16 points for power-of-two
+// lengths (their stage strides are powers of two), none for 3 * 2^p lengths (strides that are
+// multiples of 3 already spread over the banks). Chosen by counting shared-memory wavefronts of
+// every stage's load and store pattern.
+template <int N> struct Pad { static constexpr int shift = (N % 3 == 0) ? 0 : (N == 64 ? 2 : 4); };
+template <int N> __device__ __forceinline__ int padn(int i) {
+  return Pad<N>::shift ? i + (i >> Pad<N>::shift) : i;
+}
+template <int N> __host__ __device__ constexpr int pad_len() { return Pad<N>::shift ? N + (N >> Pad<N>::shift) : N; }
 
 // Radix list and lanes per line of each supported length: every radix divides the points per
 // lane E = N / LPL, so each lane runs E / R whole butterflies per stage.
@@ -38,19 +50,32 @@ template <> struct Radices<512> { static constexpr int lpl = 32, n = 3; static c
 template <> struct Radices<768> { static constexpr int lpl = 32, n = 4; static constexpr int r[4] = {3, 8, 8, 4}; };
 template <> struct Radices<1024> { static constexpr int lpl = 32, n = 4; static constexpr int r[4] = {8, 8, 8, 2}; };
 
+// Offset of stage S's twiddles in the stage-ordered table of length N: stage s (sub-transforms of
+// length NS_s = r_0 ... r_{s-1}, radix R_s) stores exp(2 pi i r k / (NS_s R_s)) at
+// k (R_s - 1) + r - 1 for k < NS_s, 0 < r < R_s; the first stage (NS = 1) needs none. Lanes of a
+// stage read consecutive k, so the table is read without bank conflicts.
+template <int N>
+__host__ __device__ constexpr int stage_off(int S) {
+  int off = 0, ns = 1;
+  for (int s = 0; s < S; ++s) {
+    if (ns > 1) off += ns * (Radices<N>::r[s] - 1);
+    ns *= Radices<N>::r[s];
+  }
+  return off;
+}
+
 // One Stockham stage of radix R after sub-transforms of length NS; v[b R + r] is input r of
-// butterfly j = lane + b LPL. tw[t * TWS] = exp(2 pi i t / N).
-template <int N, int LPL, int R, int NS, int TWS>
-__device__ __forceinline__ void stage_compute(float2* v, int lane, const float2* tw) {
+// butterfly j = lane + b LPL; stw is the stage-ordered twiddle table.
+template <int N, int LPL, int R, int NS, int OFF>
+__device__ __forceinline__ void stage_compute(float2* v, int lane, const float2* stw) {
   constexpr int BPL = N / (R * LPL);
-  constexpr int TU = N / (NS * R);
 #pragma unroll
   for (int b = 0; b < BPL; ++b) {
     const int j = lane + b * LPL;
     const int k = j % NS;
     if (NS > 1) {
 #pragma unroll
-      for (int r = 1; r < R; ++r) v[b * R + r] = c_mul(v[b * R + r], tw[r * k * TU * TWS]);
+      for (int r = 1; r < R; ++r) v[b * R + r] = c_mul(v[b * R + r], stw[OFF + k * (R - 1) + (r - 1)]);
     }
     Dft<float2, R>::run(v + b * R);
   }
@@ -65,7 +90,7 @@ __device__ __forceinline__ void stage_store(float2* buf, const float2* v, int la
     const int k = j % NS;
     const int d = (j - k) * R + k;
 #pragma unroll
-    for (int r = 0; r < R; ++r) buf[padi(d + r * NS)] = v[b * R + r];
+    for (int r = 0; r < R; ++r) buf[padn<N>(d + r * NS)] = v[b * R + r];
   }
 }
 
@@ -76,23 +101,23 @@ __device__ __forceinline__ void stage_load(const float2* buf, float2* v, int lan
   for (int b = 0; b < BPL; ++b) {
     const int j = lane + b * LPL;
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[b * R + r] = buf[padi(j + r * (N / R))];
+    for (int r = 0; r < R; ++r) v[b * R + r] = buf[padn<N>(j + r * (N / R))];
   }
 }
 
 // Inverse FFT of one line held by LPL lanes: on entry v[b R1 + r] = x[lane + b LPL + r N/R1],
 // on exit v[b RL + r] = y[lane + b LPL + r N/RL] (R1, RL the first and last radices).
-template <int N, int LPL, int S, int NS, int TWS>
-__device__ __forceinline__ void warp_fft_from(float2* v, float2* buf, int lane, const float2* tw) {
+template <int N, int LPL, int S, int NS>
+__device__ __forceinline__ void warp_fft_from(float2* v, float2* buf, int lane, const float2* stw) {
   constexpr int R = Radices<N>::r[S];
-  stage_compute<N, LPL, R, NS, TWS>(v, lane, tw);
+  stage_compute<N, LPL, R, NS, stage_off<N>(S)>(v, lane, stw);
   if constexpr (S + 1 < Radices<N>::n) {
     constexpr int R2 = Radices<N>::r[S + 1];
     __syncwarp();
     stage_store<N, LPL, R, NS>(buf, v, lane);
     __syncwarp();
     stage_load<N, LPL, R2>(buf, v, lane);
-    warp_fft_from<N, LPL, S + 1, NS * R, TWS>(v, buf, lane, tw);
+    warp_fft_from<N, LPL, S + 1, NS * R>(v, buf, lane, stw);
   }
 }
 
@@ -114,7 +139,7 @@ __global__ void __launch_bounds__(XY<N>::kThreads) xy_warp_kernel(PassArgs a) {
   constexpr int LPL = XY<N>::kLpl;
   constexpr int NT = XY<N>::kThreads;
   constexpr int E = N / LPL;
-  constexpr int kBufLd = N + N / 8;
+  constexpr int kBufLd = pad_len<N>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* tw = reinterpret_cast<float2*>(smem_raw);  // N entries exp(2 pi i t / N)
   float2* bufs = tw + N;                               // kLines x kBufLd
@@ -124,7 +149,7 @@ __global__ void __launch_bounds__(XY<N>::kThreads) xy_warp_kernel(PassArgs a) {
   const int r = g.r;
   const int w = 2 * r - 1;
   const int tid = threadIdx.x;
-  for (int i = tid; i < N; i += NT) tw[i] = static_cast<const float2*>(a.tw)[i];
+  for (int i = tid; i < N; i += NT) tw[i] = static_cast<const float2*>(a.stw)[i];
   // ---- input tile [row = k + r - 1][line]
   if (XPASS) {
     const float2* spec = static_cast<const float2*>(a.spec);
@@ -134,7 +159,7 @@ __global__ void __launch_bounds__(XY<N>::kThreads) xy_warp_kernel(PassArgs a) {
     const int hz = ng / 2 + 1;
     for (int idx = tid; idx < w * kLines; idx += NT) {
       const int l = idx & (kLines - 1);
-      const int row = idx >> 4;
+      const int row = idx >> 3;
       const int mx = row - (r - 1);
       const int kz = it.v0 + l;
       const int q = mx * mx + ky * ky + kz * kz;
@@ -155,7 +180,7 @@ __global__ void __launch_bounds__(XY<N>::kThreads) xy_warp_kernel(PassArgs a) {
     const int x = it.u;
     for (int idx = tid; idx < w * kLines; idx += NT) {
       const int l = idx & (kLines - 1);
-      const int row = idx >> 4;
+      const int row = idx >> 3;
       const int ky = row - (r - 1);
       const int kz = it.v0 + l;
       float2 val = make_float2(0.f, 0.f);
@@ -181,14 +206,14 @@ __global__ void __launch_bounds__(XY<N>::kThreads) xy_warp_kernel(PassArgs a) {
         v[b * R1 + rr] = (row >= 0 && row < w) ? tile[row * kTileLd + l] : make_float2(0.f, 0.f);
       }
     float2* buf = bufs + (size_t)l * kBufLd;
-    warp_fft_from<N, LPL, 0, 1, 1>(v, buf, lane, tw);
+    warp_fft_from<N, LPL, 0, 1>(v, buf, lane, tw);
     constexpr int RL = last_radix<N>();
     constexpr int BPLL = N / (RL * LPL);
     __syncwarp();
 #pragma unroll
     for (int b = 0; b < BPLL; ++b)
 #pragma unroll
-      for (int rr = 0; rr < RL; ++rr) buf[padi(lane + b * LPL + rr * (N / RL))] = v[b * RL + rr];
+      for (int rr = 0; rr < RL; ++rr) buf[padn<N>(lane + b * LPL + rr * (N / RL))] = v[b * RL + rr];
   }
   __syncthreads();
   // ---- output tile -> global, contiguous along k_z
@@ -203,8 +228,8 @@ __global__ void __launch_bounds__(XY<N>::kThreads) xy_warp_kernel(PassArgs a) {
   }
   for (int idx = tid; idx < N * kLines; idx += NT) {
     const int l = idx & (kLines - 1);
-    const int y = idx >> 4;
-    if (l < it.cnt) out[y * row_stride + l] = bufs[(size_t)l * kBufLd + padi(y)];
+    const int y = idx >> 3;
+    if (l < it.cnt) out[y * row_stride + l] = bufs[(size_t)l * kBufLd + padn<N>(y)];
   }
 }
 
@@ -212,17 +237,21 @@ __global__ void __launch_bounds__(XY<N>::kThreads) xy_warp_kernel(PassArgs a) {
 // Lines (shell n, x, y) of the S^3 evaluation grid in order; each group of LPL lanes takes
 // lines id, id + groups, ...
 template <int S>
-__global__ void __launch_bounds__(kZThreads) z_warp_kernel(PassArgs a, long long n_lines) {
+__global__ void __launch_bounds__(kZThreads, 4) z_warp_kernel(PassArgs a, long long n_lines) {
   constexpr int M = S / 2;
   constexpr int LPL = Radices<M>::lpl;
   constexpr int LPW = 32 / LPL;  // lines per warp at a time
   constexpr int E = M / LPL;
-  constexpr int kBufLd = M + M / 8;
+  constexpr int kBufLd = pad_len<M>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* tw = reinterpret_cast<float2*>(smem_raw);  // S entries exp(2 pi i t / S)
-  float2* bufs = tw + S;
+  float2* tw = reinterpret_cast<float2*>(smem_raw);  // M entries: stage twiddles of length M
+  float2* wk = tw + M;                               // M entries: exp(2 pi i k / S), k < M
+  float2* bufs = wk + M;
   const int tid = threadIdx.x;
-  for (int i = tid; i < S; i += kZThreads) tw[i] = static_cast<const float2*>(a.tw)[i];
+  for (int i = tid; i < M; i += kZThreads) {
+    tw[i] = static_cast<const float2*>(a.stw_half)[i];
+    wk[i] = static_cast<const float2*>(a.tw)[i];
+  }
   __syncthreads();
   const int warp = tid >> 5;
   const int sub = (tid & 31) / LPL;  // line slot inside the warp
@@ -250,10 +279,10 @@ __global__ void __launch_bounds__(kZThreads) z_warp_kernel(PassArgs a, long long
         const float2 xk = k < r ? src[k] : make_float2(0.f, 0.f);
         const float2 xm = (k > 0 && M - k < r) ? src[M - k] : make_float2(0.f, 0.f);
         const float2 e = make_float2(xk.x + xm.x, xk.y - xm.y);                // X[k] + conj X[M-k]
-        const float2 o = c_mul(make_float2(xk.x - xm.x, xk.y + xm.y), tw[k]);  // (X[k] - conj X[M-k]) W^k
+        const float2 o = c_mul(make_float2(xk.x - xm.x, xk.y + xm.y), wk[k]);  // (X[k] - conj X[M-k]) W^k
         v[b * R1 + rr] = make_float2(e.x - o.y, e.y + o.x);                    // e + i o
       }
-    warp_fft_from<M, LPL, 0, 1, 2>(v, buf, lane, tw);
+    warp_fft_from<M, LPL, 0, 1>(v, buf, lane, tw);
     float2* dst = reinterpret_cast<float2*>(static_cast<float*>(a.fields) + (long long)n * S * plane + xy * S);
 #pragma unroll
     for (int b = 0; b < BPLL; ++b)
@@ -275,12 +304,12 @@ __global__ void __launch_bounds__(kZThreads) zf_warp_kernel(PassArgs a, const fl
   constexpr int LPL = Radices<S>::lpl;
   constexpr int LPW = 32 / LPL;
   constexpr int E = S / LPL;
-  constexpr int kBufLd = S + S / 8;
+  constexpr int kBufLd = pad_len<S>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* tw = reinterpret_cast<float2*>(smem_raw);
+  float2* tw = reinterpret_cast<float2*>(smem_raw);  // stage twiddles of length S
   float2* bufs = tw + S;
   const int tid = threadIdx.x;
-  for (int i = tid; i < S; i += kZThreads) tw[i] = static_cast<const float2*>(a.tw)[i];
+  for (int i = tid; i < S; i += kZThreads) tw[i] = static_cast<const float2*>(a.stw)[i];
   __syncthreads();
   const int warp = tid >> 5;
   const int sub = (tid & 31) / LPL;
@@ -304,7 +333,7 @@ __global__ void __launch_bounds__(kZThreads) zf_warp_kernel(PassArgs a, const fl
     for (int b = 0; b < BPL; ++b)
 #pragma unroll
       for (int rr = 0; rr < R1; ++rr) v[b * R1 + rr] = make_float2(src[lane + b * LPL + rr * (S / R1)], 0.f);
-    warp_fft_from<S, LPL, 0, 1, 1>(v, buf, lane, tw);
+    warp_fft_from<S, LPL, 0, 1>(v, buf, lane, tw);
     float2* dst = static_cast<float2*>(a.g2) + g.g2_off + xy * r;
 #pragma unroll
     for (int b = 0; b < BPLL; ++b)
@@ -323,7 +352,7 @@ __global__ void __launch_bounds__(XY<N>::kThreads) xyf_warp_kernel(PassArgs a, f
   constexpr int LPL = XY<N>::kLpl;
   constexpr int NT = XY<N>::kThreads;
   constexpr int E = N / LPL;
-  constexpr int kBufLd = N + N / 8;
+  constexpr int kBufLd = pad_len<N>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* tw = reinterpret_cast<float2*>(smem_raw);  // N
   float2* bufs = tw + N;                               // kLines x kBufLd
@@ -333,7 +362,7 @@ __global__ void __launch_bounds__(XY<N>::kThreads) xyf_warp_kernel(PassArgs a, f
   const int r = g.r;
   const int w = 2 * r - 1;
   const int tid = threadIdx.x;
-  for (int i = tid; i < N; i += NT) tw[i] = static_cast<const float2*>(a.tw)[i];
+  for (int i = tid; i < N; i += NT) tw[i] = static_cast<const float2*>(a.stw)[i];
   // ---- input tile [position along the line][line], contiguous along k_z in memory
   const float2* src;
   long long row_stride;
@@ -346,7 +375,7 @@ __global__ void __launch_bounds__(XY<N>::kThreads) xyf_warp_kernel(PassArgs a, f
   }
   for (int idx = tid; idx < N * kLines; idx += NT) {
     const int l = idx & (kLines - 1);
-    const int y = idx >> 4;
+    const int y = idx >> 3;
     tile[y * kTileLd + l] = l < it.cnt ? src[y * row_stride + l] : make_float2(0.f, 0.f);
   }
   __syncthreads();
@@ -361,14 +390,14 @@ __global__ void __launch_bounds__(XY<N>::kThreads) xyf_warp_kernel(PassArgs a, f
 #pragma unroll
       for (int rr = 0; rr < R1; ++rr) v[b * R1 + rr] = tile[(lane + b * LPL + rr * (N / R1)) * kTileLd + l];
     float2* buf = bufs + (size_t)l * kBufLd;
-    warp_fft_from<N, LPL, 0, 1, 1>(v, buf, lane, tw);
+    warp_fft_from<N, LPL, 0, 1>(v, buf, lane, tw);
     constexpr int RL = last_radix<N>();
     constexpr int BPLL = N / (RL * LPL);
     __syncwarp();
 #pragma unroll
     for (int b = 0; b < BPLL; ++b)
 #pragma unroll
-      for (int rr = 0; rr < RL; ++rr) buf[padi(lane + b * LPL + rr * (N / RL))] = v[b * RL + rr];
+      for (int rr = 0; rr < RL; ++rr) buf[padn<N>(lane + b * LPL + rr * (N / RL))] = v[b * RL + rr];
   }
   __syncthreads();
   // ---- keep the positions |k| <= r - 1: row = k + r - 1
@@ -380,12 +409,12 @@ __global__ void __launch_bounds__(XY<N>::kThreads) xyf_warp_kernel(PassArgs a, f
     const int iy = ky < 0 ? ky + ng : ky;
     for (int idx = tid; idx < w * kLines; idx += NT) {
       const int l = idx & (kLines - 1);
-      const int row = idx >> 4;
+      const int row = idx >> 3;
       const int kx = row - (r - 1);
       const int kz = it.v0 + l;
       const int q = kx * kx + ky * ky + kz * kz;
       if (l < it.cnt && q >= g.qlo && q < g.qhi) {
-        float2 val = bufs[(size_t)l * kBufLd + padi(kx < 0 ? kx + N : kx)];
+        float2 val = bufs[(size_t)l * kBufLd + padn<N>(kx < 0 ? kx + N : kx)];
         float fac = scale;
         if (a.rsd) fac *= (float)(1.0 + a.beta * (double)(kz * kz) / (double)q);
         const int ix = kx < 0 ? kx + ng : kx;
@@ -396,9 +425,9 @@ __global__ void __launch_bounds__(XY<N>::kThreads) xyf_warp_kernel(PassArgs a, f
     float2* dst = static_cast<float2*>(a.g1) + g.g1_off + (long long)it.u * w * r + it.v0;
     for (int idx = tid; idx < w * kLines; idx += NT) {
       const int l = idx & (kLines - 1);
-      const int row = idx >> 4;
+      const int row = idx >> 3;
       const int ky = row - (r - 1);
-      if (l < it.cnt) dst[(long long)row * r + l] = bufs[(size_t)l * kBufLd + padi(ky < 0 ? ky + N : ky)];
+      if (l < it.cnt) dst[(long long)row * r + l] = bufs[(size_t)l * kBufLd + padn<N>(ky < 0 ? ky + N : ky)];
     }
   }
 }
@@ -406,7 +435,7 @@ __global__ void __launch_bounds__(XY<N>::kThreads) xyf_warp_kernel(PassArgs a, f
 template <int N, bool XPASS>
 bsp_status launch_xyf(const PassArgs& a, int n_items, float scale, cudaStream_t s) {
   if (n_items == 0) return BSP_OK;
-  const size_t smem = ((size_t)N + (size_t)kLines * (N + N / 8) + (size_t)N * kTileLd) * sizeof(float2);
+  const size_t smem = ((size_t)N + (size_t)kLines * pad_len<N>() + (size_t)N * kTileLd) * sizeof(float2);
   BSP_CUDA(cudaFuncSetAttribute(xyf_warp_kernel<N, XPASS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   xyf_warp_kernel<N, XPASS><<<n_items, XY<N>::kThreads, smem, s>>>(a, scale);
   BSP_CUDA(cudaGetLastError());
@@ -416,7 +445,7 @@ bsp_status launch_xyf(const PassArgs& a, int n_items, float scale, cudaStream_t 
 template <int S>
 bsp_status launch_zf(const PassArgs& a, const float* gfield, long long n_lines, int n_sm, cudaStream_t s) {
   constexpr int LPW = 32 / Radices<S>::lpl;
-  const size_t smem = ((size_t)S + (size_t)(kZThreads / 32) * LPW * (S + S / 8)) * sizeof(float2);
+  const size_t smem = ((size_t)S + (size_t)(kZThreads / 32) * LPW * pad_len<S>()) * sizeof(float2);
   BSP_CUDA(cudaFuncSetAttribute(zf_warp_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   BSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, zf_warp_kernel<S>, kZThreads, smem));
@@ -434,7 +463,7 @@ bsp_status launch_xy(const PassArgs& a, int n_items, cudaStream_t s) {
   if (n_items == 0) return BSP_OK;
   // the tile holds 2 r - 1 rows of the largest shell
   const size_t smem =
-      ((size_t)N + (size_t)kLines * (N + N / 8) + (size_t)(2 * a.rmax) * kTileLd) * sizeof(float2);
+      ((size_t)N + (size_t)kLines * pad_len<N>() + (size_t)(2 * a.rmax) * kTileLd) * sizeof(float2);
   BSP_CUDA(cudaFuncSetAttribute(xy_warp_kernel<N, XPASS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   xy_warp_kernel<N, XPASS><<<n_items, XY<N>::kThreads, smem, s>>>(a);
   BSP_CUDA(cudaGetLastError());
@@ -445,7 +474,7 @@ template <int S>
 bsp_status launch_z(const PassArgs& a, long long n_lines, int n_sm, cudaStream_t s) {
   constexpr int M = S / 2;
   constexpr int LPW = 32 / Radices<M>::lpl;
-  const size_t smem = ((size_t)S + (size_t)(kZThreads / 32) * LPW * (M + M / 8)) * sizeof(float2);
+  const size_t smem = ((size_t)2 * M + (size_t)(kZThreads / 32) * LPW * pad_len<M>()) * sizeof(float2);
   BSP_CUDA(cudaFuncSetAttribute(z_warp_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   BSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, z_warp_kernel<S>, kZThreads, smem));
@@ -459,6 +488,32 @@ bsp_status launch_z(const PassArgs& a, long long n_lines, int n_sm, cudaStream_t
 }
 
 }  // namespace
+
+template <int N>
+static void stage_table(std::vector<float2>& out) {
+  out.clear();
+  int ns = 1;
+  for (int s = 0; s < Radices<N>::n; ++s) {
+    const int R = Radices<N>::r[s];
+    if (ns > 1)
+      for (int k = 0; k < ns; ++k)
+        for (int r = 1; r < R; ++r) {
+          const double ang = 2.0 * 3.14159265358979323846 * (double)r * (double)k / (double)(ns * R);
+          out.push_back(make_float2((float)cos(ang), (float)sin(ang)));
+        }
+    ns *= R;
+  }
+  out.resize(N, make_float2(0.f, 0.f));
+}
+
+bool warp_stage_table(int n, std::vector<float2>& out) {
+  switch (n) {
+#define X(N) case N: stage_table<N>(out); return true;
+    X(64) X(96) X(128) X(192) X(256) X(384) X(512) X(768) X(1024)
+#undef X
+  }
+  return false;
+}
 
 bool warp_fft_supported(int s) {
   return s == 128 || s == 192 || s == 256 || s == 384 || s == 512 || s == 768 || s == 1024;

@@ -63,7 +63,9 @@ struct PassArgs {
   void* g1;               // X-pass output
   void* g2;               // Y-pass output
   void* fields;           // Z-pass output, [n][x][y][z] real T
-  const void* tw;         // twiddles exp(+2 pi i j / ng), j < ng (complex T)
+  const void* tw;         // twiddles exp(+2 pi i j / ngs), j < ngs (complex T)
+  const void* stw;        // warp kernels: stage-ordered twiddles of length ngs (float2)
+  const void* stw_half;   // warp kernels: stage-ordered twiddles of length ngs / 2
   const ShellGeom* geom;  // per shell
   const Item* items;      // work items of this pass
   int ng;                 // side of the input spectrum's grid
@@ -77,6 +79,8 @@ struct PassArgs {
 // Warp-per-line FP32 passes (bispec_fft_warp.cu) for evaluation grids 2^p and 3 * 2^p from
 // 128 to 1024; X/Y items hold at most warp_fft_lines() lines.
 bool warp_fft_supported(int ngs);
+// Stage-ordered twiddle table of a warp FFT length (n entries, zero padded); false if unsupported.
+bool warp_stage_table(int n, std::vector<float2>& out);
 int warp_fft_lines();
 bsp_status launch_warp_xpass(const PassArgs& a, int n_items, cudaStream_t s);
 bsp_status launch_warp_ypass(const PassArgs& a, int n_items, cudaStream_t s);
