@@ -343,16 +343,16 @@ def run_ours(args, w):
     npairs = len({(int(a), int(b)) for a, b in zip(tr["a"], tr["b"])})
     nvox = float(plan.ng_eval) ** 3
     if dname == "contract" and args.precision == "mixed_bf16x3":
-        # split-BF16 GEMM work: 3 MMAs x 2 flops per (pair, shell column, voxel); shell columns are
-        # padded to the MMA N of 32 (or 64)
-        ncols = 32 if plan.n_shells <= 32 else 64
-        tflop = 3 * 2 * npairs * ncols * nvox / 1e12
+        # split-BF16 GEMM work from the library: 3 MMAs x 2 flops per (pair, padded shell column,
+        # voxel), summed over the contraction levels
+        tflop = wf[dom] / 1e12
         ach = tflop / tdom
         roof = {"bound": "tensor", "kernel": "contract_tc_kernel (tcgen05 kind::f16, bf16x3)",
                 "achieved": round(ach, 2), "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
                 "frac": round(ach / pk["bf16_tflops"], 4),
                 "peak_kind": f"{pk_kind} bf16_tflops (burst, cuBLAS)",
-                "work": f"3 x 2 x {npairs} pairs x {ncols} shell columns x {plan.ng_eval}^3 voxels",
+                "work": f"3 x 2 x pairs x 32 shell columns x g^3 voxels over the contraction levels "
+                        f"({tflop:.3f} TFLOP per estimate)",
                 "traffic": ncu_traffic(dname, args.workload, args.precision)}
     elif dname == "contract" and args.precision == "fp32":
         sm_mhz = pk.get("sm_max_mhz", 2070.0)

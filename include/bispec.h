@@ -126,7 +126,9 @@ BSP_API bsp_status bsp_shell_fields(bsp_plan* plan, const void* spec, void* fiel
 /* Triple-product sums, the numerator of Eq. (2.7): msum[t] = sum_x d_a d_b d_c over the ng^3 grid
  * for every kept bin t, from shell fields on the evaluation grid laid out as bsp_shell_fields
  * writes them (device, read-only, 16-byte aligned); computed as (ng / S)^3 times the sum over
- * the S^3 grid. msum: device, n_triplets doubles. Uses the plan's contraction (bsp_precision). */
+ * the S^3 grid (bins whose triple products fit a coarser divisor grid g of S are summed on that
+ * grid, sampled from the given fields, times (ng / g)^3). msum: device, n_triplets doubles. Uses
+ * the plan's contraction (bsp_precision). */
 BSP_API bsp_status bsp_contract(bsp_plan* plan, const void* fields, double* msum, void* stream);
 
 /* The whole estimator on one field, Eqs. (2.7)-(2.11) and the (mu, t) map:
@@ -217,7 +219,10 @@ BSP_API bsp_status bsp_timing_read(bsp_plan* plan, double* ms, int* n_calls, lon
 
 /* Algorithmic work of one bsp_estimate per stage: bytes[s] that stage must move to or from
  * device memory (reads of the non-zero inputs it needs plus its outputs, each once) and
- * flops[s] of its arithmetic core (0 where it is negligible). Host-side, no GPU work. */
+ * flops[s] of its arithmetic core (0 where it is negligible): for the contraction, one product
+ * per pair and one multiply-add per bin and voxel on CUDA cores, or 3 x 2 x pairs x padded shell
+ * columns x voxels for the split-BF16 tensor-core GEMM, summed over the contraction levels.
+ * Host-side, no GPU work. */
 BSP_API bsp_status bsp_plan_stage_work(const bsp_plan* plan, double* bytes, double* flops);
 
 /* Limits of bsp_triple_sums_noalloc (its scratch array has a fixed size). */

@@ -72,6 +72,34 @@ struct DevBuf {
 
 using namespace bsp;
 
+// One level of the contraction: the bins whose triple products hold only wavevectors with
+// components below g_l are summed on a g_l^3 grid (a divisor of the evaluation grid, sampled from
+// its fields with stride S / g_l), exact for the same reason the evaluation grid is.
+struct ContractLevel {
+  int g = 0;                  // grid side
+  int stride = 1;             // evaluation-grid side / g
+  double scale = 1.0;         // (ng / g)^3
+  std::vector<int> shells;    // global shell of each local field index
+  std::vector<int> bins;      // kept bins (global indices, ascending) summed on this level
+  bool top = false;           // uses the plan's fields directly (all shells, global indices)
+  void* fields = nullptr;     // [shells][g^3] for lower levels
+  int* d_shells = nullptr;
+  // CUDA-core contraction
+  Tile* d_tiles = nullptr;
+  int2* d_pairs = nullptr;
+  int* d_map = nullptr;       // [ntiles][16] global bin index or -1
+  int ntiles = 0, gridx = 0;
+  double* partial = nullptr;
+  // tensor-core contraction
+  int np = 0, mtiles = 0, gridy = 0;
+  long long vpb = 0;
+  int2* d_tc_pairs = nullptr;
+  int* d_tc_map = nullptr;
+  int* d_tc_bins = nullptr;
+  double* tc_partial = nullptr;
+  long long nvox() const { return (long long)g * g * g; }
+};
+
 struct bsp_plan {
   // description
   int ng = 0, ns = 0, n_mu = 0, n_t = 0, rsd = 0, prec = 0;
@@ -113,6 +141,7 @@ struct bsp_plan {
   Item *d_wxi = nullptr, *d_wyi = nullptr;
   int nwxi = 0, nwyi = 0;
   int rmax = 0;
+  std::vector<ContractLevel> levels;
   // tensor-core contraction (BSP_MIXED_BF16X3)
   int tc_np = 0, tc_mtiles = 0, tc_gridy = 0;
   long long tc_vpb = 0;
@@ -233,7 +262,8 @@ void make_items(const bsp_plan* p, int lines_xy, int lines_z, std::vector<Item>&
 
 // Tiles of up to 4 consecutive pairs x 4 consecutive c over a list of bins sorted by (a, b, c).
 void make_tiles(const std::vector<int>& ta, const std::vector<int>& tb, const std::vector<int>& tc,
-                std::vector<int2>& pairs, std::vector<Tile>& tiles, std::vector<int>& map) {
+                std::vector<int2>& pairs, std::vector<Tile>& tiles, std::vector<int>& map,
+                const std::vector<int>* ids = nullptr) {
   pairs.clear(); tiles.clear(); map.clear();
   std::vector<std::vector<std::pair<int, int>>> pc;  // per pair: (c, bin)
   for (size_t t = 0; t < ta.size(); ++t) {
@@ -241,7 +271,7 @@ void make_tiles(const std::vector<int>& ta, const std::vector<int>& tb, const st
       pairs.push_back(make_int2(ta[t], tb[t]));
       pc.emplace_back();
     }
-    pc.back().push_back({tc[t], (int)t});
+    pc.back().push_back({tc[t], ids ? (*ids)[t] : (int)t});
   }
   const int np = (int)pairs.size();
   for (int p0 = 0; p0 < np; p0 += 4) {
@@ -291,14 +321,16 @@ bsp_status run_passes(const bsp_plan* p, const void* spec, int rsd, void* tw, vo
   return launch_zpass<T>(a, nzi, lines_z, s);
 }
 
-int pick_gridx(const bsp_plan* p, int ntiles) {
+int pick_gridx_n(int n_sm, int ntiles, long long nvox) {
   const int gy = (ntiles + 255) / 256;
-  int gx = (4 * p->n_sm) / std::max(gy, 1);
+  int gx = (4 * n_sm) / std::max(gy, 1);
   gx = std::max(gx, 1);
-  const long long chunks = (p->nvox() + 63) / 64;
+  const long long chunks = (nvox + 63) / 64;
   if (gx > chunks) gx = (int)chunks;
   return gx;
 }
+
+int pick_gridx(const bsp_plan* p, int ntiles) { return pick_gridx_n(p->n_sm, ntiles, p->nvox()); }
 
 bsp_status validate(const bsp_plan_desc* d) {
   if (!d) return fail(BSP_ERR_INVALID_ARG, "desc is NULL");
@@ -435,6 +467,107 @@ long long g2_elems(const bsp_plan* p) {
   return g.g2_off + (long long)p->ngs * p->ngs * g.r;
 }
 
+// Contraction levels (see ContractLevel): each pair (a, b) of the kept bins goes to the smallest
+// divisor g of the evaluation grid (g % 8 == 0, g >= 16) above r_a + r_b + r_cmax - 3, the largest
+// wavevector component of its triple products.
+bsp_status build_levels(bsp_plan* p, cudaStream_t s) {
+  const int S = p->ngs;
+  std::vector<std::pair<int, std::vector<int>>> by_g;  // ascending g
+  auto bins_of = [&](int g) -> std::vector<int>& {
+    for (auto& e : by_g)
+      if (e.first == g) return e.second;
+    by_g.push_back({g, {}});
+    return by_g.back().second;
+  };
+  size_t t = 0;
+  while (t < p->trips.size()) {
+    size_t u = t;
+    int cmax = 0;
+    while (u < p->trips.size() && p->trips[u].a == p->trips[t].a && p->trips[u].b == p->trips[t].b) {
+      cmax = std::max(cmax, p->trips[u].c);
+      ++u;
+    }
+    const int need = p->geom[p->trips[t].a].r + p->geom[p->trips[t].b].r + p->geom[cmax].r - 2;
+    int g = S;
+    for (int cand = 16; cand < S; cand += 8)
+      if (S % cand == 0 && cand >= need) { g = cand; break; }
+    std::vector<int>& v = bins_of(g);
+    for (size_t w = t; w < u; ++w) v.push_back((int)w);
+    t = u;
+  }
+  std::sort(by_g.begin(), by_g.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
+  const size_t re = p->elem();
+  bsp_status st;
+  for (auto& e : by_g) {
+    ContractLevel L;
+    L.g = e.first;
+    L.stride = S / L.g;
+    const double f = (double)p->ng / (double)L.g;
+    L.scale = f * f * f;
+    L.top = L.g == S;
+    L.bins = e.second;
+    std::vector<int> loc(p->ns, -1);
+    if (L.top) {
+      for (int n = 0; n < p->ns; ++n) { L.shells.push_back(n); loc[n] = n; }
+    } else {
+      std::vector<char> used(p->ns, 0);
+      for (int b : L.bins) used[p->trips[b].a] = used[p->trips[b].b] = used[p->trips[b].c] = 1;
+      for (int n = 0; n < p->ns; ++n)
+        if (used[n]) { loc[n] = (int)L.shells.size(); L.shells.push_back(n); }
+    }
+    const int nsh = (int)L.shells.size();
+    std::vector<int> la, lb, lc;
+    for (int b : L.bins) {
+      la.push_back(loc[p->trips[b].a]);
+      lb.push_back(loc[p->trips[b].b]);
+      lc.push_back(loc[p->trips[b].c]);
+    }
+    std::vector<int2> pairs;
+    std::vector<Tile> tiles;
+    std::vector<int> map;
+    make_tiles(la, lb, lc, pairs, tiles, map, &L.bins);
+    void* tmp = nullptr;
+    if (p->prec == BSP_MIXED_BF16X3) {
+      L.np = tc_padded_shells(nsh);
+      const int np = (int)pairs.size();
+      L.mtiles = (np + 127) / 128;
+      std::vector<int2> pab((size_t)std::max(L.mtiles, 1) * 128, make_int2(-1, -1));
+      for (int i = 0; i < np; ++i) pab[i] = pairs[i];
+      std::vector<int> tmap(L.bins.size());
+      int pi = -1;
+      for (size_t i = 0; i < L.bins.size(); ++i) {
+        if (i == 0 || la[i] != la[i - 1] || lb[i] != lb[i - 1]) ++pi;
+        tmap[i] = pi * L.np + lc[i];
+      }
+      const long long chunks = L.nvox() / kTcVoxelChunk;
+      long long gy = std::min<long long>(std::max(1, p->n_sm), chunks);
+      L.vpb = ((chunks + gy - 1) / gy) * kTcVoxelChunk;
+      L.gridy = (int)((L.nvox() + L.vpb - 1) / L.vpb);
+      if ((st = dev_upload(p, pab, &L.d_tc_pairs, s)) != BSP_OK) return st;
+      if ((st = dev_upload(p, tmap, &L.d_tc_map, s)) != BSP_OK) return st;
+      if ((st = dev_upload(p, L.bins, &L.d_tc_bins, s)) != BSP_OK) return st;
+      if ((st = dev_alloc(p, tc_partial_doubles(std::max(L.mtiles, 1), L.gridy, L.np) * sizeof(double), &tmp)) != BSP_OK)
+        return st;
+      L.tc_partial = static_cast<double*>(tmp);
+    } else {
+      L.ntiles = (int)tiles.size();
+      L.gridx = pick_gridx_n(p->n_sm, L.ntiles, L.nvox());
+      if ((st = dev_upload(p, tiles, &L.d_tiles, s)) != BSP_OK) return st;
+      if ((st = dev_upload(p, pairs, &L.d_pairs, s)) != BSP_OK) return st;
+      if ((st = dev_upload(p, map, &L.d_map, s)) != BSP_OK) return st;
+      if ((st = dev_alloc(p, (size_t)std::max(L.gridx, 1) * std::max(L.ntiles, 1) * 16 * sizeof(double), &tmp)) != BSP_OK)
+        return st;
+      L.partial = static_cast<double*>(tmp);
+    }
+    if (!L.top) {
+      if ((st = dev_upload(p, L.shells, &L.d_shells, s)) != BSP_OK) return st;
+      if ((st = dev_alloc(p, (size_t)nsh * (size_t)L.nvox() * re, &L.fields)) != BSP_OK) return st;
+    }
+    p->levels.push_back(std::move(L));
+  }
+  return BSP_OK;
+}
+
 // Eq. (2.10) in FP64 on the GPU for the candidate bins: T_abc = sum_x i_a i_b i_c.
 bsp_status count_triangles(bsp_plan* p, const std::vector<int>& ca, const std::vector<int>& cb,
                            const std::vector<int>& cc, std::vector<double>& tsum, cudaStream_t s) {
@@ -501,40 +634,78 @@ bsp_status count_triangles(bsp_plan* p, const std::vector<int>& ca, const std::v
 template <typename T>
 bsp_status run_contract(bsp_plan* p, const void* fields, double* msum, cudaStream_t s, cudaEvent_t mid) {
   bsp_status st;
-  if (p->prec == BSP_MIXED_BF16X3) {
-    TcArgs a{};
-    a.fields = static_cast<const float*>(fields);
-    a.nvox = p->nvox();
-    a.ns = p->ns;
-    a.np = p->tc_np;
-    a.pair_ab = p->d_tc_pairs;
-    a.n_mtiles = p->tc_mtiles;
-    a.gridy = p->tc_gridy;
-    a.vox_per_block = p->tc_vpb;
-    a.partial = p->tc_partial;
-    a.error = p->d_error;
-    st = launch_contract_tc(a, s);
+  // contraction kernels of every level (lower levels first sample their fields)
+  for (ContractLevel& L : p->levels) {
+    const void* f = fields;
+    if (!L.top) {
+      st = launch_decimate<T>(fields, p->ngs, L.d_shells, (int)L.shells.size(), L.fields, L.g, L.stride, p->n_sm, s);
+      if (st != BSP_OK) return st;
+      f = L.fields;
+    }
+    if (p->prec == BSP_MIXED_BF16X3) {
+      TcArgs a{};
+      a.fields = static_cast<const float*>(f);
+      a.nvox = L.nvox();
+      a.ns = (int)L.shells.size();
+      a.np = L.np;
+      a.pair_ab = L.d_tc_pairs;
+      a.n_mtiles = L.mtiles;
+      a.gridy = L.gridy;
+      a.vox_per_block = L.vpb;
+      a.partial = L.tc_partial;
+      a.error = p->d_error;
+      st = launch_contract_tc(a, s);
+    } else {
+      ContractArgs c{};
+      c.fields = f;
+      c.nvox = L.nvox();
+      c.ns = (int)L.shells.size();
+      c.tiles = L.d_tiles;
+      c.pairs = L.d_pairs;
+      c.tile_map = L.d_map;
+      c.ntiles = L.ntiles;
+      c.gridx = L.gridx;
+      c.partial = L.partial;
+      c.msum = msum;
+      c.n_out = (int)L.bins.size();
+      c.scale = L.scale;
+      st = launch_contract_simt<T>(c, s);
+    }
     if (st != BSP_OK) return st;
-    if (mid) BSP_CUDA(cudaEventRecord(mid, s));
-    return launch_reduce_tc(a, p->d_tc_map, (int)p->trips.size(), msum, p->sum_scale, s);
   }
-  ContractArgs c{};
-  c.fields = fields;
-  c.nvox = p->nvox();
-  c.ns = p->ns;
-  c.tiles = p->d_tiles;
-  c.pairs = p->d_pairs;
-  c.tile_map = p->d_map;
-  c.ntiles = p->ntiles;
-  c.gridx = p->gridx;
-  c.partial = p->partial;
-  c.msum = msum;
-  c.n_out = (int)p->trips.size();
-  c.scale = p->sum_scale;
-  st = launch_contract_simt<T>(c, s);
-  if (st != BSP_OK) return st;
   if (mid) BSP_CUDA(cudaEventRecord(mid, s));
-  return launch_reduce_partials(c, s);
+  // cross-block sums of every level, scaled to the ng^3 grid
+  for (ContractLevel& L : p->levels) {
+    if (p->prec == BSP_MIXED_BF16X3) {
+      TcArgs a{};
+      a.np = L.np;
+      a.n_mtiles = L.mtiles;
+      a.gridy = L.gridy;
+      a.partial = L.tc_partial;
+      st = launch_reduce_tc(a, L.d_tc_map, L.d_tc_bins, (int)L.bins.size(), msum, L.scale, s);
+    } else {
+      ContractArgs c{};
+      c.tile_map = L.d_map;
+      c.ntiles = L.ntiles;
+      c.gridx = L.gridx;
+      c.partial = L.partial;
+      c.msum = msum;
+      c.scale = L.scale;
+      st = launch_reduce_partials(c, s);
+    }
+    if (st != BSP_OK) return st;
+  }
+  return BSP_OK;
+}
+
+// Kernels launched by run_contract.
+int contract_launches(const bsp_plan* p) {
+  int n = 0;
+  for (const ContractLevel& L : p->levels) {
+    const bool work = p->prec == BSP_MIXED_BF16X3 ? L.mtiles > 0 : L.ntiles > 0;
+    n += (!L.top) + 2 * work;
+  }
+  return n;
 }
 
 // The three pass launches of an estimate on the plan's buffers; ev (optional) receives an event
@@ -612,8 +783,7 @@ bsp_status estimate_impl(bsp_plan* p, const void* spec, double* b_trip, double* 
   if (rec) {
     BSP_CUDA(cudaEventRecord(ev[5], s));
     p->timing_calls += 1;
-    const int ncontract = p->prec == BSP_MIXED_BF16X3 ? 2 * (p->tc_mtiles > 0) : 2 * (p->ntiles > 0);
-    p->launches += (p->nxi > 0) + (p->nyi > 0) + (p->nzi > 0) + ncontract + 1;
+    p->launches += (p->nxi > 0) + (p->nyi > 0) + (p->nzi > 0) + contract_launches(p) + 1;
   }
   return BSP_OK;
 }
@@ -642,12 +812,22 @@ void stage_work(const bsp_plan* p, double* bytes, double* flops) {
     bytes[BSP_STAGE_YPASS] += ce * ng * (double)xlines + ce * ng * ng * r;
     bytes[BSP_STAGE_ZPASS] += ce * ng * ng * r + re * ng * ng * ng;
   }
-  // pairs of the kept bins
-  long long npairs = 0;
-  for (size_t t = 0; t < p->trips.size(); ++t)
-    if (t == 0 || p->trips[t].a != p->trips[t - 1].a || p->trips[t].b != p->trips[t - 1].b) npairs += 1;
-  bytes[BSP_STAGE_CONTRACT] = re * (double)p->ns * ng * ng * ng;
-  flops[BSP_STAGE_CONTRACT] = ((double)npairs + 2.0 * (double)p->trips.size()) * ng * ng * ng;
+  // contraction levels: fields read once per level (lower levels also read their samples of the
+  // evaluation grid and write them), work per level on its g^3 grid
+  for (const ContractLevel& L : p->levels) {
+    const double nv = (double)L.nvox();
+    const double nsh = (double)L.shells.size();
+    long long npairs = 0;
+    for (size_t i = 0; i < L.bins.size(); ++i) {
+      const bsp_triplet& a = p->trips[L.bins[i]];
+      if (i == 0 || a.a != p->trips[L.bins[i - 1]].a || a.b != p->trips[L.bins[i - 1]].b) npairs += 1;
+    }
+    bytes[BSP_STAGE_CONTRACT] += re * nsh * nv * (L.top ? 1.0 : 3.0);
+    if (p->prec == BSP_MIXED_BF16X3)
+      flops[BSP_STAGE_CONTRACT] += 3.0 * 2.0 * (double)npairs * (double)L.np * nv;  // split-BF16 GEMM
+    else
+      flops[BSP_STAGE_CONTRACT] += ((double)npairs + 2.0 * (double)L.bins.size()) * nv;
+  }
   bytes[BSP_STAGE_FINALIZE] = 8.0 * (double)p->trips.size() * 3 + 8.0 * p->n_cells();
 }
 
@@ -821,12 +1001,6 @@ bsp_status bsp_plan_create(const bsp_plan_desc* desc, void* stream, bsp_plan** o
   make_items(p, p->lines_xy, p->lines_z, xi, yi, zi);
   p->nxi = (int)xi.size(); p->nyi = (int)yi.size(); p->nzi = (int)zi.size();
   const size_t ce = p->prec == BSP_FP64 ? sizeof(double2) : sizeof(float2);
-  std::vector<int2> pairs;
-  std::vector<Tile> tiles;
-  std::vector<int> map;
-  make_tiles(ka, kb, kc, pairs, tiles, map);
-  p->ntiles = (int)tiles.size();
-  p->gridx = pick_gridx(p, p->ntiles);
   std::vector<int> cptr(p->n_cells() + 1, 0), cidx;
   {
     std::vector<std::vector<int>> cells(p->n_cells());
@@ -864,44 +1038,14 @@ bsp_status bsp_plan_create(const bsp_plan_desc* desc, void* stream, bsp_plan** o
   TRY(dev_alloc(p, g1_elems(p) * ce, &p->g1));
   TRY(dev_alloc(p, g2_elems(p) * ce, &p->g2));
   TRY(dev_alloc(p, p->field_bytes(), &p->fields));
-  TRY(dev_upload(p, tiles, &p->d_tiles, s));
-  TRY(dev_upload(p, pairs, &p->d_pairs, s));
-  TRY(dev_upload(p, map, &p->d_map, s));
+  TRY(build_levels(p, s));
   void* tmp = nullptr;
-  TRY(dev_alloc(p, (size_t)std::max(p->gridx, 1) * std::max(p->ntiles, 1) * 16 * sizeof(double), &tmp));
-  p->partial = static_cast<double*>(tmp);
   TRY(dev_alloc(p, std::max<size_t>(p->trips.size(), 1) * sizeof(double), &tmp));
   p->msum = static_cast<double*>(tmp);
   TRY(dev_upload(p, kt, &p->tsum, s));
   {
     std::vector<int> zero(1, 0);
     TRY(dev_upload(p, zero, &p->d_error, s));
-  }
-  if (p->prec == BSP_MIXED_BF16X3) {
-    p->tc_np = tc_padded_shells(p->ns);
-    const int np = (int)pairs.size();
-    p->tc_mtiles = (np + 127) / 128;
-    std::vector<int2> pab((size_t)std::max(p->tc_mtiles, 1) * 128, make_int2(-1, -1));
-    for (int i = 0; i < np; ++i) pab[i] = pairs[i];
-    // map of every kept bin to its (pair row, c) entry
-    std::vector<int> tmap(p->trips.size());
-    {
-      int pi = -1;
-      for (size_t t = 0; t < p->trips.size(); ++t) {
-        if (t == 0 || p->trips[t].a != p->trips[t - 1].a || p->trips[t].b != p->trips[t - 1].b) ++pi;
-        tmap[t] = pi * p->tc_np + p->trips[t].c;
-      }
-    }
-    const long long chunks = p->nvox() / kTcVoxelChunk;
-    // one block per SM and voxel range; the M tiles of one range run side by side (L2 reuse)
-    long long gy = std::max(1, p->n_sm);
-    gy = std::min(gy, chunks);
-    p->tc_vpb = ((chunks + gy - 1) / gy) * kTcVoxelChunk;
-    p->tc_gridy = (int)((p->nvox() + p->tc_vpb - 1) / p->tc_vpb);
-    TRY(dev_upload(p, pab, &p->d_tc_pairs, s));
-    TRY(dev_upload(p, tmap, &p->d_tc_map, s));
-    TRY(dev_alloc(p, tc_partial_doubles(std::max(p->tc_mtiles, 1), p->tc_gridy, p->tc_np) * sizeof(double), &tmp));
-    p->tc_partial = static_cast<double*>(tmp);
   }
   TRY(dev_upload(p, cptr, &p->cell_ptr, s));
   TRY(dev_upload(p, cidx, &p->cell_idx, s));

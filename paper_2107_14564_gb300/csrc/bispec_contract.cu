@@ -8,6 +8,8 @@
 // HBM serves every tile of the block. FP32 plans accumulate in FP32 over kFlushChunks chunks
 // and then add into FP64; FP64 plans accumulate in FP64. Blocks write FP64 partial sums,
 // which a second kernel adds in a fixed order (deterministic results).
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace bsp {
@@ -123,6 +125,40 @@ bsp_status launch_reduce_partials(const ContractArgs& a, cudaStream_t s) {
 
 template bsp_status launch_contract_simt<float>(const ContractArgs&, cudaStream_t);
 template bsp_status launch_contract_simt<double>(const ContractArgs&, cudaStream_t);
+
+// ---------------------------------------------------------------- level fields
+// dst[j][x][y][z] = src[shells[j]][t x][t y][t z]: the fields of a coarser level sampled from the
+// evaluation grid (side S) with stride t.
+template <typename T>
+__global__ void decimate_kernel(const T* __restrict__ src, int S, const int* __restrict__ shells, int nsh,
+                                T* __restrict__ dst, int g, int t) {
+  const long long per = (long long)g * g * g;
+  const long long total = per * nsh;
+  const long long plane = (long long)S * S;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(i / per);
+    const long long v = i - (long long)j * per;
+    const int x = (int)(v / ((long long)g * g));
+    const int y = (int)((v / g) % g);
+    const int z = (int)(v % g);
+    dst[i] = src[(long long)shells[j] * plane * S + ((long long)x * t * S + (long long)y * t) * S + (long long)z * t];
+  }
+}
+
+template <typename T>
+bsp_status launch_decimate(const void* src, int S, const int* shells, int nsh, void* dst, int g, int t, int n_sm,
+                           cudaStream_t s) {
+  const long long total = (long long)g * g * g * nsh;
+  if (total == 0) return BSP_OK;
+  long long blocks = std::min<long long>((total + 255) / 256, 16LL * n_sm);
+  decimate_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(static_cast<const T*>(src), S, shells, nsh, static_cast<T*>(dst),
+                                                     g, t);
+  BSP_CUDA(cudaGetLastError());
+  return BSP_OK;
+}
+template bsp_status launch_decimate<float>(const void*, int, const int*, int, void*, int, int, int, cudaStream_t);
+template bsp_status launch_decimate<double>(const void*, int, const int*, int, void*, int, int, int, cudaStream_t);
 
 // ---------------------------------------------------------------- finalize
 // b_trip[t] = norm msum[t] / tsum[t]                     (Eq. (2.7) with Eq. (2.10))

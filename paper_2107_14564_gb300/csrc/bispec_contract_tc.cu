@@ -300,14 +300,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) contract_tc_kernel(TcArgs a) {
 }
 
 // msum[t] = scale * sum over voxel blocks of partial[y][map[t]], blocks in order.
-__global__ void reduce_tc_kernel(const double* partial, int gridy, long long stride, const int* map, int n_out,
-                                 double* msum, double scale) {
+__global__ void reduce_tc_kernel(const double* partial, int gridy, long long stride, const int* map, const int* bins,
+                                 int n_out, double* msum, double scale) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n_out) return;
   const long long off = map[t];
   double s = 0.0;
   for (int y = 0; y < gridy; ++y) s += partial[(long long)y * stride + off];
-  msum[t] = scale * s;
+  msum[bins ? bins[t] : t] = scale * s;
 }
 
 }  // namespace
@@ -334,11 +334,11 @@ bsp_status launch_contract_tc(const TcArgs& a, cudaStream_t s) {
   return BSP_OK;
 }
 
-bsp_status launch_reduce_tc(const TcArgs& a, const int* map, int n_out, double* msum, double scale,
-                            cudaStream_t s) {
+bsp_status launch_reduce_tc(const TcArgs& a, const int* map, const int* bins, int n_out, double* msum,
+                            double scale, cudaStream_t s) {
   if (a.n_mtiles == 0 || n_out == 0) return BSP_OK;
   const long long stride = (long long)a.n_mtiles * 128 * a.np;
-  reduce_tc_kernel<<<(n_out + 255) / 256, 256, 0, s>>>(a.partial, a.gridy, stride, map, n_out, msum, scale);
+  reduce_tc_kernel<<<(n_out + 255) / 256, 256, 0, s>>>(a.partial, a.gridy, stride, map, bins, n_out, msum, scale);
   BSP_CUDA(cudaGetLastError());
   return BSP_OK;
 }

@@ -136,6 +136,9 @@ struct ContractArgs {
 template <typename T>
 bsp_status launch_contract_simt(const ContractArgs& a, cudaStream_t s);
 bsp_status launch_reduce_partials(const ContractArgs& a, cudaStream_t s);
+template <typename T>
+bsp_status launch_decimate(const void* src, int S, const int* shells, int nsh, void* dst, int g, int t, int n_sm,
+                           cudaStream_t s);
 
 struct FinalizeArgs {
   const double* msum;
@@ -167,9 +170,10 @@ struct TcArgs {
 int tc_padded_shells(int ns);
 size_t tc_partial_doubles(int n_mtiles, int gridy, int np);
 bsp_status launch_contract_tc(const TcArgs& a, cudaStream_t s);
-// msum[t] = scale * sum_y partial[y][map[t]], map[t] = (mtile * 128 + row) * np + c of bin t
-bsp_status launch_reduce_tc(const TcArgs& a, const int* map, int n_out, double* msum, double scale,
-                            cudaStream_t s);
+// msum[bins[t]] = scale * sum_y partial[y][map[t]], t < n_out, map[t] = (mtile * 128 + row) * np + c
+// (bins may be null: identity)
+bsp_status launch_reduce_tc(const TcArgs& a, const int* map, const int* bins, int n_out, double* msum,
+                            double scale, cudaStream_t s);
 
 // ---------------------------------------------------------------- gradient (bispec_grad.cu)
 bsp_status launch_build_w(const double* g, const double* cnorm, const int* ptr, const int* idx, int n_entries,
