@@ -40,6 +40,10 @@ WORKLOADS = {
 WORKLOADS["prof384"] = dict(ng=384, box=384.0, n_index=1.5, f_ng=0.05, beta=None, ns=8, top=96.0,
                             n_mu=10, n_t=10, seed=11,
                             text="profiling case: Ng=384 L=384, 8 linear shells k_f..k_Nyq/2, 10x10 cells")
+WORKLOADS["prof256"] = dict(ng=256, box=256.0, n_index=1.5, f_ng=0.05, beta=None, ns=32, top=64.0,
+                            n_mu=10, n_t=10, seed=12,
+                            text="profiling case: Ng=256 L=256, 32 linear shells k_f..k_Nyq/2, 10x10 cells "
+                                 "(full 128-row tensor-core tiles on a 256^3 grid, 2 GB of fields)")
 WORKLOADS["batch64"] = dict(text="64 seeded quadratic NG fields (P=k^-1.5, f=0.05) on uneven grids: 16 x 128^3, "
                                  "24 x 192^3, 24 x 256^3 (L=Ng), 16 linear shells k_f..k_Nyq/2 each, 10x10 "
                                  "(mu,t) cells, one captured CUDA graph",

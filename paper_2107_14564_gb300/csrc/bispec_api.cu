@@ -82,8 +82,10 @@ struct ContractLevel {
   std::vector<int> shells;    // global shell of each local field index
   std::vector<int> bins;      // kept bins (global indices, ascending) summed on this level
   bool top = false;           // uses the plan's fields directly (all shells, global indices)
-  void* fields = nullptr;     // [shells][g^3] for lower levels
-  int* d_shells = nullptr;
+  void* fields = nullptr;     // [shells][g^3] for lower levels (split planes [2][shells][g^3] for
+                              // tensor-core plans)
+  int* d_shells = nullptr;    // source field of each destination field of the level sampling
+  CUtensorMap tmap{};         // tensor-core plans: the level's split fields
   // CUDA-core contraction
   Tile* d_tiles = nullptr;
   int2* d_pairs = nullptr;
@@ -123,6 +125,11 @@ struct bsp_plan {
   Item *d_xi = nullptr, *d_yi = nullptr, *d_zi = nullptr;
   int nxi = 0, nyi = 0, nzi = 0;
   void *g1 = nullptr, *g2 = nullptr, *fields = nullptr;
+  void* fields32 = nullptr;  // tensor-core plans on the generic passes: FP32 fields before the split
+  // tensor-core plans on the warp passes: the Z pass also writes the coarser levels' fields
+  ZLevel* d_zlev = nullptr;
+  uint32_t* d_zmask = nullptr;
+  int n_zlev = 0;
   // contraction tables (kept bins)
   Tile* d_tiles = nullptr;
   int2* d_pairs = nullptr;
@@ -291,6 +298,60 @@ void make_tiles(const std::vector<int>& ta, const std::vector<int>& tb, const st
       for (int k = 0; k < 16; ++k) map.push_back(m[k]);
     }
   }
+}
+
+// Rows of the tensor-core contraction: pair i goes to row row_of[i] of a group of 32 rows (one
+// TMEM lane quarter, whose generator threads read the two fields of their pairs from shared
+// memory in one instruction each). Field n's rows sit in 16-byte bank group n mod 8 of every
+// 128-byte line, so a group whose first fields a take distinct values mod 8, and its second
+// fields b too, is served in one pass per load; a window of 8 (16) consecutive field indices
+// costs one (two). Groups are taken greedily: the window of 8 or 16 consecutive a by 8 or 16
+// consecutive b with the most unassigned pairs (at most 32) per pass. Returns the group count.
+int assign_tc_rows(const std::vector<int2>& pairs, int nsh, std::vector<int>& row_of) {
+  const int n = nsh;
+  std::vector<int> id((size_t)n * n, -1);
+  for (size_t i = 0; i < pairs.size(); ++i) id[(size_t)pairs[i].x * n + pairs[i].y] = (int)i;
+  row_of.assign(pairs.size(), -1);
+  std::vector<int> pre((size_t)(n + 1) * (n + 1), 0);
+  auto cnt = [&](int a0, int b0, int wa, int wb) {
+    const int a1 = std::min(n, a0 + wa), b1 = std::min(n, b0 + wb);
+    a0 = std::max(a0, 0);
+    b0 = std::max(b0, 0);
+    if (a1 <= a0 || b1 <= b0) return 0;
+    return pre[(size_t)a1 * (n + 1) + b1] - pre[(size_t)a0 * (n + 1) + b1] - pre[(size_t)a1 * (n + 1) + b0] +
+           pre[(size_t)a0 * (n + 1) + b0];
+  };
+  static const int shapes[4][2] = {{8, 8}, {8, 16}, {16, 8}, {16, 16}};
+  size_t left = pairs.size();
+  int groups = 0;
+  while (left > 0) {
+    for (int a = 0; a < n; ++a)
+      for (int b = 0; b < n; ++b) {
+        const int i = id[(size_t)a * n + b];
+        pre[(size_t)(a + 1) * (n + 1) + b + 1] = pre[(size_t)a * (n + 1) + b + 1] + pre[(size_t)(a + 1) * (n + 1) + b] -
+                                                 pre[(size_t)a * (n + 1) + b] + (i >= 0 && row_of[i] < 0);
+      }
+    double best = -1.0;
+    int ba = 0, bb = 0, bwa = 8, bwb = 8;
+    for (const auto& sh : shapes) {
+      const int wa = sh[0], wb = sh[1];
+      const double c = wa / 8 + wb / 8;
+      for (int a0 = 1 - wa; a0 < n; ++a0)
+        for (int b0 = 1 - wb; b0 < n; ++b0) {
+          const double v = std::min(32, cnt(a0, b0, wa, wb)) / c;
+          if (v > best) { best = v; ba = a0; bb = b0; bwa = wa; bwb = wb; }
+        }
+    }
+    int lane = 0;
+    for (int a = std::max(ba, 0); a < std::min(n, ba + bwa) && lane < 32; ++a)
+      for (int b = std::max(bb, 0); b < std::min(n, bb + bwb) && lane < 32; ++b) {
+        const int i = id[(size_t)a * n + b];
+        if (i >= 0 && row_of[i] < 0) row_of[i] = groups * 32 + lane++;
+      }
+    left -= (size_t)lane;
+    ++groups;
+  }
+  return groups;
 }
 
 // Shell fields of one precision: X, Y, Z passes for every shell.
@@ -498,6 +559,8 @@ bsp_status build_levels(bsp_plan* p, cudaStream_t s) {
   std::sort(by_g.begin(), by_g.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
   const size_t re = p->elem();
   bsp_status st;
+  std::vector<ZLevel> zl;  // levels the split Z pass writes
+  std::vector<int> zt;     // their strides
   for (auto& e : by_g) {
     ContractLevel L;
     L.g = e.first;
@@ -530,14 +593,16 @@ bsp_status build_levels(bsp_plan* p, cudaStream_t s) {
     if (p->prec == BSP_MIXED_BF16X3) {
       L.np = tc_padded_shells(nsh);
       const int np = (int)pairs.size();
-      L.mtiles = (np + 127) / 128;
+      std::vector<int> row_of;
+      const int groups = assign_tc_rows(pairs, nsh, row_of);
+      L.mtiles = (groups + 3) / 4;
       std::vector<int2> pab((size_t)std::max(L.mtiles, 1) * 128, make_int2(-1, -1));
-      for (int i = 0; i < np; ++i) pab[i] = pairs[i];
+      for (int i = 0; i < np; ++i) pab[row_of[i]] = pairs[i];
       std::vector<int> tmap(L.bins.size());
       int pi = -1;
       for (size_t i = 0; i < L.bins.size(); ++i) {
         if (i == 0 || la[i] != la[i - 1] || lb[i] != lb[i - 1]) ++pi;
-        tmap[i] = pi * L.np + lc[i];
+        tmap[i] = row_of[pi] * L.np + lc[i];
       }
       const long long chunks = L.nvox() / kTcVoxelChunk;
       long long gy = std::min<long long>(std::max(1, p->n_sm), chunks);
@@ -560,10 +625,39 @@ bsp_status build_levels(bsp_plan* p, cudaStream_t s) {
       L.partial = static_cast<double*>(tmp);
     }
     if (!L.top) {
-      if ((st = dev_upload(p, L.shells, &L.d_shells, s)) != BSP_OK) return st;
+      std::vector<int> src = L.shells;
+      if (p->prec == BSP_MIXED_BF16X3)  // split planes: high parts, then low parts (ns planes later)
+        for (int n : L.shells) src.push_back(p->ns + n);
+      if ((st = dev_upload(p, src, &L.d_shells, s)) != BSP_OK) return st;
       if ((st = dev_alloc(p, (size_t)nsh * (size_t)L.nvox() * re, &L.fields)) != BSP_OK) return st;
     }
+    if (p->prec == BSP_MIXED_BF16X3 && L.mtiles > 0) {
+      st = encode_split_map(&L.tmap, L.top ? p->fields : L.fields, L.nvox(), nsh, L.np);
+      if (st != BSP_OK) return st;
+    }
+    if (p->prec == BSP_MIXED_BF16X3 && p->warp_fft && !L.top) {
+      ZLevel z{};
+      z.dst = static_cast<uint16_t*>(L.fields);
+      z.lo_off = (long long)nsh * L.nvox();
+      int* dloc = nullptr;
+      if ((st = dev_upload(p, loc, &dloc, s)) != BSP_OK) return st;
+      z.loc = dloc;
+      z.g = L.g;
+      z.rt = 1.0f / (float)L.stride;
+      zl.push_back(z);
+      zt.push_back(L.stride);
+    }
     p->levels.push_back(std::move(L));
+  }
+  if (!zl.empty()) {
+    if (zl.size() > 32) return fail(BSP_ERR_NOT_SUPPORTED, "more than 32 contraction levels");
+    std::vector<uint32_t> mask(S, 0u);
+    for (int i = 0; i < S; ++i)
+      for (size_t l = 0; l < zt.size(); ++l)
+        if (i % zt[l] == 0) mask[i] |= 1u << l;
+    if ((st = dev_upload(p, zl, &p->d_zlev, s)) != BSP_OK) return st;
+    if ((st = dev_upload(p, mask, &p->d_zmask, s)) != BSP_OK) return st;
+    p->n_zlev = (int)zl.size();
   }
   return BSP_OK;
 }
@@ -630,21 +724,28 @@ bsp_status count_triangles(bsp_plan* p, const std::vector<int>& ca, const std::v
 }
 
 // The contraction of a plan (CUDA cores or tensor cores) and its cross-block sums into msum.
-// `mid` (optional) is recorded between the two launches.
+// `mid` (optional) is recorded between the two launches. Tensor-core plans read the split fields
+// of the plan's own buffer (their tensor maps point there): `fields` must be p->fields.
 template <typename T>
-bsp_status run_contract(bsp_plan* p, const void* fields, double* msum, cudaStream_t s, cudaEvent_t mid) {
+bsp_status run_contract(bsp_plan* p, const void* fields, double* msum, cudaStream_t s, cudaEvent_t mid,
+                        bool levels_ready = false) {
   bsp_status st;
   // contraction kernels of every level (lower levels first sample their fields)
   for (ContractLevel& L : p->levels) {
     const void* f = fields;
-    if (!L.top) {
-      st = launch_decimate<T>(fields, p->ngs, L.d_shells, (int)L.shells.size(), L.fields, L.g, L.stride, p->n_sm, s);
+    if (!L.top && levels_ready) {
+      f = L.fields;  // written by the split Z pass
+    } else if (!L.top) {
+      if (p->prec == BSP_MIXED_BF16X3)  // split planes sampled as 2 x shells bf16 fields
+        st = launch_decimate<uint16_t>(fields, p->ngs, L.d_shells, 2 * (int)L.shells.size(), L.fields, L.g, L.stride,
+                                       p->n_sm, s);
+      else
+        st = launch_decimate<T>(fields, p->ngs, L.d_shells, (int)L.shells.size(), L.fields, L.g, L.stride, p->n_sm, s);
       if (st != BSP_OK) return st;
       f = L.fields;
     }
     if (p->prec == BSP_MIXED_BF16X3) {
       TcArgs a{};
-      a.fields = static_cast<const float*>(f);
       a.nvox = L.nvox();
       a.ns = (int)L.shells.size();
       a.np = L.np;
@@ -654,7 +755,7 @@ bsp_status run_contract(bsp_plan* p, const void* fields, double* msum, cudaStrea
       a.vox_per_block = L.vpb;
       a.partial = L.tc_partial;
       a.error = p->d_error;
-      st = launch_contract_tc(a, s);
+      st = launch_contract_tc(a, &L.tmap, s);
     } else {
       ContractArgs c{};
       c.fields = f;
@@ -703,15 +804,17 @@ int contract_launches(const bsp_plan* p) {
   int n = 0;
   for (const ContractLevel& L : p->levels) {
     const bool work = p->prec == BSP_MIXED_BF16X3 ? L.mtiles > 0 : L.ntiles > 0;
-    n += (!L.top) + 2 * work;
+    const bool sampled = !L.top && !(p->prec == BSP_MIXED_BF16X3 && p->n_zlev > 0);  // else the Z pass did it
+    n += sampled + 2 * work;
   }
   return n;
 }
 
 // The three pass launches of an estimate on the plan's buffers; ev (optional) receives an event
-// after the X and after the Y pass, and after the Z pass.
+// after the X and after the Y pass, and after the Z pass. split: write split fields (the layout
+// of the tensor-core contraction, see TcArgs) instead of FP32 ones.
 template <typename T>
-bsp_status plan_passes(bsp_plan* p, const void* spec, void* fields, cudaStream_t s, cudaEvent_t* ev) {
+bsp_status plan_passes(bsp_plan* p, const void* spec, void* fields, cudaStream_t s, cudaEvent_t* ev, bool split = false) {
   PassArgs a{};
   a.spec = spec;
   a.g1 = p->g1;
@@ -728,6 +831,12 @@ bsp_status plan_passes(bsp_plan* p, const void* spec, void* fields, cudaStream_t
   a.stw_half = p->d_stw_half;
   bsp_status st;
   if (std::is_same<T, float>::value && p->warp_fft) {
+    a.split_lo = split ? (long long)p->ns * p->nvox() / 2 : 0;
+    if (split) {
+      a.zlev = p->d_zlev;
+      a.zmask = p->d_zmask;
+      a.n_zlev = p->n_zlev;
+    }
     a.items = p->d_wxi;
     st = launch_warp_xpass(a, p->nwxi, s);
     if (st != BSP_OK) return st;
@@ -752,8 +861,14 @@ bsp_status plan_passes(bsp_plan* p, const void* spec, void* fields, cudaStream_t
   if (ev) BSP_CUDA(cudaEventRecord(ev[1], s));
   a.items = p->d_zi;
   a.st = p->st_half;
+  if (split) a.fields = p->fields32;
   st = launch_zpass<T>(a, p->nzi, p->lines_z, s);
   if (st != BSP_OK) return st;
+  if (split) {
+    st = launch_split_fields(static_cast<const float*>(p->fields32), static_cast<uint32_t*>(fields),
+                             (long long)p->ns * p->nvox() / 2, p->n_sm, s);
+    if (st != BSP_OK) return st;
+  }
   if (ev) BSP_CUDA(cudaEventRecord(ev[2], s));
   return BSP_OK;
 }
@@ -763,9 +878,10 @@ bsp_status estimate_impl(bsp_plan* p, const void* spec, double* b_trip, double* 
   const bool rec = p->timing_on && p->timing_calls < p->timing_max;
   cudaEvent_t* ev = rec ? &p->events[(size_t)p->timing_calls * (BSP_N_STAGES + 1)] : nullptr;
   if (rec) BSP_CUDA(cudaEventRecord(ev[0], s));
-  bsp_status st = plan_passes<T>(p, spec, p->fields, s, rec ? ev + 1 : nullptr);
+  const bool split = p->prec == BSP_MIXED_BF16X3;
+  bsp_status st = plan_passes<T>(p, spec, p->fields, s, rec ? ev + 1 : nullptr, split);
   if (st != BSP_OK) return st;
-  st = run_contract<T>(p, p->fields, p->msum, s, rec ? ev[4] : nullptr);
+  st = run_contract<T>(p, p->fields, p->msum, s, rec ? ev[4] : nullptr, split && p->warp_fft);
   if (st != BSP_OK) return st;
   FinalizeArgs f{};
   f.msum = p->msum;
@@ -783,7 +899,8 @@ bsp_status estimate_impl(bsp_plan* p, const void* spec, double* b_trip, double* 
   if (rec) {
     BSP_CUDA(cudaEventRecord(ev[5], s));
     p->timing_calls += 1;
-    p->launches += (p->nxi > 0) + (p->nyi > 0) + (p->nzi > 0) + contract_launches(p) + 1;
+    const int passes = p->warp_fft ? 3 : (p->nxi > 0) + (p->nyi > 0) + (p->nzi > 0) + (split ? 1 : 0);
+    p->launches += passes + contract_launches(p) + 1;
   }
   return BSP_OK;
 }
@@ -1038,6 +1155,7 @@ bsp_status bsp_plan_create(const bsp_plan_desc* desc, void* stream, bsp_plan** o
   TRY(dev_alloc(p, g1_elems(p) * ce, &p->g1));
   TRY(dev_alloc(p, g2_elems(p) * ce, &p->g2));
   TRY(dev_alloc(p, p->field_bytes(), &p->fields));
+  if (p->prec == BSP_MIXED_BF16X3 && !p->warp_fft) TRY(dev_alloc(p, p->field_bytes(), &p->fields32));
   TRY(build_levels(p, s));
   void* tmp = nullptr;
   TRY(dev_alloc(p, std::max<size_t>(p->trips.size(), 1) * sizeof(double), &tmp));
@@ -1102,6 +1220,13 @@ bsp_status bsp_contract(bsp_plan* p, const void* fields, double* msum, void* str
   if ((reinterpret_cast<uintptr_t>(fields) & 15) != 0) return fail(BSP_ERR_INVALID_ARG, "fields must be 16-byte aligned");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (p->prec == BSP_FP64) return run_contract<double>(p, fields, msum, s, nullptr);
+  if (p->prec == BSP_MIXED_BF16X3) {
+    // the tensor-core contraction reads split fields from the plan's buffer
+    const bsp_status st = launch_split_fields(static_cast<const float*>(fields), static_cast<uint32_t*>(p->fields),
+                                              (long long)p->ns * p->nvox() / 2, p->n_sm, s);
+    if (st != BSP_OK) return st;
+    return run_contract<float>(p, p->fields, msum, s, nullptr);
+  }
   return run_contract<float>(p, fields, msum, s, nullptr);
 }
 

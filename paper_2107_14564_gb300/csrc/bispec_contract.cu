@@ -159,6 +159,7 @@ bsp_status launch_decimate(const void* src, int S, const int* shells, int nsh, v
 }
 template bsp_status launch_decimate<float>(const void*, int, const int*, int, void*, int, int, int, cudaStream_t);
 template bsp_status launch_decimate<double>(const void*, int, const int*, int, void*, int, int, int, cudaStream_t);
+template bsp_status launch_decimate<uint16_t>(const void*, int, const int*, int, void*, int, int, int, cudaStream_t);
 
 // ---------------------------------------------------------------- finalize
 // b_trip[t] = norm msum[t] / tsum[t]                     (Eq. (2.7) with Eq. (2.10))

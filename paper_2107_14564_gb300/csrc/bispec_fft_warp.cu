@@ -15,6 +15,7 @@
 //     W^k directly from global memory and writes z[n] = x[2n] + i x[2n+1] straight to the field.
 #include "common.cuh"
 #include "fft_radix.cuh"
+#include "tc_ptx.cuh"
 
 #include <math.h>
 
@@ -247,11 +248,14 @@ __global__ void __launch_bounds__(kZThreads, 4) z_warp_kernel(PassArgs a, long l
   float2* tw = reinterpret_cast<float2*>(smem_raw);  // M entries: stage twiddles of length M
   float2* wk = tw + M;                               // M entries: exp(2 pi i k / S), k < M
   float2* bufs = wk + M;
+  uint32_t* zmask = reinterpret_cast<uint32_t*>(bufs + (size_t)(kZThreads / 32) * LPW * kBufLd);  // S entries
   const int tid = threadIdx.x;
   for (int i = tid; i < M; i += kZThreads) {
     tw[i] = static_cast<const float2*>(a.stw_half)[i];
     wk[i] = static_cast<const float2*>(a.tw)[i];
   }
+  if (a.n_zlev > 0)
+    for (int i = tid; i < S; i += kZThreads) zmask[i] = a.zmask[i];
   __syncthreads();
   const int warp = tid >> 5;
   const int sub = (tid & 31) / LPL;  // line slot inside the warp
@@ -283,11 +287,66 @@ __global__ void __launch_bounds__(kZThreads, 4) z_warp_kernel(PassArgs a, long l
         v[b * R1 + rr] = make_float2(e.x - o.y, e.y + o.x);                    // e + i o
       }
     warp_fft_from<M, LPL, 0, 1>(v, buf, lane, tw);
-    float2* dst = reinterpret_cast<float2*>(static_cast<float*>(a.fields) + (long long)n * S * plane + xy * S);
+    const long long off = (long long)n * S * plane + xy * S;  // first voxel of the line
+    if (a.split_lo == 0) {
+      float2* dst = reinterpret_cast<float2*>(static_cast<float*>(a.fields) + off);
 #pragma unroll
-    for (int b = 0; b < BPLL; ++b)
+      for (int b = 0; b < BPLL; ++b)
 #pragma unroll
-      for (int rr = 0; rr < RL; ++rr) dst[lane + b * LPL + rr * (M / RL)] = v[b * RL + rr];
+        for (int rr = 0; rr < RL; ++rr) dst[lane + b * LPL + rr * (M / RL)] = v[b * RL + rr];
+    } else {
+      // split fields: bf16 high parts of the voxel pair (2k, 2k + 1) in one word, low parts in
+      // the word split_lo further
+      uint32_t* hi = static_cast<uint32_t*>(a.fields) + off / 2;
+#pragma unroll
+      for (int b = 0; b < BPLL; ++b)
+#pragma unroll
+        for (int rr = 0; rr < RL; ++rr) {
+          const float2 x = v[b * RL + rr];
+          uint32_t h, l;
+          ptx::split_bf16x2(ptx::f2_pack(x.x, x.y), h, l);
+          const int k = lane + b * LPL + rr * (M / RL);
+          hi[k] = h;
+          hi[a.split_lo + k] = l;
+        }
+      // coarser levels: lines with x and y multiples of the level's stride, every t-th voxel
+      if (a.n_zlev > 0) {
+        const int x = (int)(xy / S);
+        const int y = (int)(xy - (long long)x * S);
+        uint32_t mask = zmask[x] & zmask[y];
+        while (mask != 0) {
+          const int l = __ffs(mask) - 1;
+          mask &= mask - 1;
+          const ZLevel L = a.zlev[l];
+          const int j = L.loc[n];
+          if (j < 0) continue;
+          const uint32_t bit = 1u << l;
+          uint16_t* lh = L.dst + (((long long)j * L.g + __float2int_rn(x * L.rt)) * L.g + __float2int_rn(y * L.rt)) * L.g;
+#pragma unroll
+          for (int b = 0; b < BPLL; ++b)
+#pragma unroll
+            for (int rr = 0; rr < RL; ++rr) {
+              const int k = lane + b * LPL + rr * (M / RL);
+              const bool e0 = (zmask[2 * k] & bit) != 0, e1 = (zmask[2 * k + 1] & bit) != 0;
+              if (e0 || e1) {
+                const float2 x2 = v[b * RL + rr];
+                uint32_t h, lo;
+                ptx::split_bf16x2(ptx::f2_pack(x2.x, x2.y), h, lo);
+                if (e0) {
+                  const int zz = __float2int_rn((2 * k) * L.rt);
+                  lh[zz] = (uint16_t)(h & 0xFFFFu);
+                  lh[L.lo_off + zz] = (uint16_t)(lo & 0xFFFFu);
+                }
+                if (e1) {
+                  const int zz = __float2int_rn((2 * k + 1) * L.rt);
+                  lh[zz] = (uint16_t)(h >> 16);
+                  lh[L.lo_off + zz] = (uint16_t)(lo >> 16);
+                }
+              }
+            }
+        }
+      }
+    }
   }
 }
 
@@ -474,7 +533,8 @@ template <int S>
 bsp_status launch_z(const PassArgs& a, long long n_lines, int n_sm, cudaStream_t s) {
   constexpr int M = S / 2;
   constexpr int LPW = 32 / Radices<M>::lpl;
-  const size_t smem = ((size_t)2 * M + (size_t)(kZThreads / 32) * LPW * pad_len<M>()) * sizeof(float2);
+  const size_t smem = ((size_t)2 * M + (size_t)(kZThreads / 32) * LPW * pad_len<M>()) * sizeof(float2) +
+                      (a.n_zlev > 0 ? (size_t)S * sizeof(uint32_t) : 0);
   BSP_CUDA(cudaFuncSetAttribute(z_warp_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   BSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, z_warp_kernel<S>, kZThreads, smem));

@@ -1,6 +1,7 @@
 // Shared device helpers and the internal plan layout of the bispectrum library.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -74,6 +75,22 @@ struct PassArgs {
   double beta;
   FftStages st;           // stage list of this pass's line length
   int rmax;               // largest r of all shells
+  long long split_lo;     // warp Z pass: 0 writes FP32 fields; otherwise bf16 high parts [n][x][y][z]
+                          // at `fields` and low parts split_lo 32-bit words further (split fields)
+  // split warp Z pass: also write the split fields of the coarser contraction levels
+  const struct ZLevel* zlev;  // n_zlev levels
+  const uint32_t* zmask;      // [ngs]: bit l set when coordinate i is a multiple of level l's stride
+  int n_zlev;
+};
+
+// A coarser contraction level the split Z pass samples: voxel (x, y, z) of the evaluation grid with
+// all three coordinates multiples of the stride t goes to (x / t, y / t, z / t) of the level.
+struct ZLevel {
+  uint16_t* dst;      // [2][nsh][g^3] split planes
+  long long lo_off;   // nsh * g^3: offset of the low plane (elements)
+  const int* loc;     // [ns]: the level's field index of each shell, -1 if unused
+  int g;              // level side
+  float rt;           // 1 / t (t divides every coordinate it is applied to: exact after rounding)
 };
 
 // Warp-per-line FP32 passes (bispec_fft_warp.cu) for evaluation grids 2^p and 3 * 2^p from
@@ -155,8 +172,10 @@ bsp_status launch_finalize(const FinalizeArgs& a, cudaStream_t s);
 
 // ---------------------------------------------------------------- tensor-core contraction
 constexpr int kTcVoxelChunk = 128;  // voxels per pipeline stage of the tensor-core contraction
+// Split fields: d = d_hi + d_lo with d_hi = bf16(d) and d_lo = bf16(d - d_hi), stored as two
+// bf16 planes [2][ns][nvox] (high parts first). The contraction reads them through a 3D tensor
+// map (voxel, shell, part) with 64 x NP x 1 boxes and the 128-byte swizzle.
 struct TcArgs {
-  const float* fields;      // [ns][nvox] FP32, 16-byte aligned
   long long nvox;           // multiple of kTcVoxelChunk
   int ns;
   int np;                   // shells padded for the MMA N dimension (32 or 64)
@@ -169,7 +188,11 @@ struct TcArgs {
 };
 int tc_padded_shells(int ns);
 size_t tc_partial_doubles(int n_mtiles, int gridy, int np);
-bsp_status launch_contract_tc(const TcArgs& a, cudaStream_t s);
+bsp_status launch_contract_tc(const TcArgs& a, const CUtensorMap* tmap, cudaStream_t s);
+// Encode the tensor map of split fields at `base` ([2][rows][nvox] bf16) for NP-row boxes.
+bsp_status encode_split_map(CUtensorMap* map, void* base, long long nvox, int rows, int np);
+// Split FP32 fields [ns][nvox] into bf16 planes: hi (n words of two values) at dst, lo at dst + n.
+bsp_status launch_split_fields(const float* src, uint32_t* dst, long long n_words, int n_sm, cudaStream_t s);
 // msum[bins[t]] = scale * sum_y partial[y][map[t]], t < n_out, map[t] = (mtile * 128 + row) * np + c
 // (bins may be null: identity)
 bsp_status launch_reduce_tc(const TcArgs& a, const int* map, const int* bins, int n_out, double* msum,

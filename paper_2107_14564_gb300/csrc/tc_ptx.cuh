@@ -65,6 +65,19 @@ __device__ __forceinline__ void bulk_g2s(void* smem_dst, const void* gmem_src, u
       : "memory");
 }
 
+// 3D tiled TMA load (coordinate x innermost) into shared memory; completes on the mbarrier with
+// the box's byte count. tmap: generic address of a __grid_constant__ CUtensorMap.
+__device__ __forceinline__ void tma_load_3d(void* smem_dst, const void* tmap, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(smem_u32(smem_dst)),
+      "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void prefetch_tmap(const void* tmap) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(tmap) : "memory");
+}
+
 // ------------------------------------------------------------------ proxy fences
 // Make generic-proxy shared-memory writes visible to the async proxy (the tensor core).
 __device__ __forceinline__ void fence_proxy_async_smem() {
@@ -134,6 +147,13 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
   d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
   d |= (uint64_t)1 << 46;
   return d;
+}
+
+// The same for K-major operands that a tiled TMA wrote with the 128-byte swizzle: rows of 128
+// bytes (64 bf16 along K), 8-row atoms of 1024 bytes (SBO) aligned to 1024 bytes; a K step of 16
+// elements inside an atom advances the start address by 32 bytes. LBO is unused by this layout.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr, uint32_t sbo) {
+  return smem_desc(saddr, 16u, sbo) | ((uint64_t)2 << 61);
 }
 
 // Instruction descriptor of kind::f16 with BF16 A and B, FP32 D, both K-major.
