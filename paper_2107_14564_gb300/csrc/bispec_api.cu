@@ -98,6 +98,7 @@ struct ContractLevel {
   int2* d_tc_pairs = nullptr;
   int* d_tc_map = nullptr;
   int* d_tc_bins = nullptr;
+  std::vector<int> tc_off;    // partial-sum entry of each of the level's bins
   double* tc_partial = nullptr;
   long long nvox() const { return (long long)g * g * g; }
 };
@@ -127,6 +128,7 @@ struct bsp_plan {
   void *g1 = nullptr, *g2 = nullptr, *fields = nullptr;
   void* fields32 = nullptr;  // tensor-core plans on the generic passes: FP32 fields before the split
   // tensor-core plans on the warp passes: the Z pass also writes the coarser levels' fields
+  TcBin* d_tc_bins = nullptr;  // tensor-core plans: where each kept bin's partial sums are
   ZLevel* d_zlev = nullptr;
   uint32_t* d_zmask = nullptr;
   int n_zlev = 0;
@@ -300,58 +302,43 @@ void make_tiles(const std::vector<int>& ta, const std::vector<int>& tb, const st
   }
 }
 
-// Rows of the tensor-core contraction: pair i goes to row row_of[i] of a group of 32 rows (one
-// TMEM lane quarter, whose generator threads read the two fields of their pairs from shared
-// memory in one instruction each). Field n's rows sit in 16-byte bank group n mod 8 of every
-// 128-byte line, so a group whose first fields a take distinct values mod 8, and its second
-// fields b too, is served in one pass per load; a window of 8 (16) consecutive field indices
-// costs one (two). Groups are taken greedily: the window of 8 or 16 consecutive a by 8 or 16
-// consecutive b with the most unassigned pairs (at most 32) per pass. Returns the group count.
-int assign_tc_rows(const std::vector<int2>& pairs, int nsh, std::vector<int>& row_of) {
-  const int n = nsh;
-  std::vector<int> id((size_t)n * n, -1);
-  for (size_t i = 0; i < pairs.size(); ++i) id[(size_t)pairs[i].x * n + pairs[i].y] = (int)i;
+// Rows of the tensor-core contraction: pair i goes to row row_of[i]. Every row costs the same
+// generation work, so pairs are packed densely; their order only matters for shared-memory bank
+// conflicts. A generator thread reads 16 bytes of field a and of field b of its row per load, and
+// a 128-bit load is served in four phases of 8 consecutive lanes; field n's 16 bytes sit in bank
+// group n mod 8 of their 128-byte line (the TMA's swizzle), so a phase is conflict-free when its
+// distinct a take distinct values mod 8, and its distinct b too. Rows are filled 8 at a time by
+// first fit over the pairs in (a, b) order. Padding rows of a phase repeat its first pair, encoded
+// as (-a - 1, -b - 1) (a broadcast, never read back). Returns the number of rows (multiple of 8).
+int assign_tc_rows(const std::vector<int2>& pairs, std::vector<int>& row_of, std::vector<int2>& rows) {
   row_of.assign(pairs.size(), -1);
-  std::vector<int> pre((size_t)(n + 1) * (n + 1), 0);
-  auto cnt = [&](int a0, int b0, int wa, int wb) {
-    const int a1 = std::min(n, a0 + wa), b1 = std::min(n, b0 + wb);
-    a0 = std::max(a0, 0);
-    b0 = std::max(b0, 0);
-    if (a1 <= a0 || b1 <= b0) return 0;
-    return pre[(size_t)a1 * (n + 1) + b1] - pre[(size_t)a0 * (n + 1) + b1] - pre[(size_t)a1 * (n + 1) + b0] +
-           pre[(size_t)a0 * (n + 1) + b0];
-  };
-  static const int shapes[4][2] = {{8, 8}, {8, 16}, {16, 8}, {16, 16}};
-  size_t left = pairs.size();
-  int groups = 0;
-  while (left > 0) {
-    for (int a = 0; a < n; ++a)
-      for (int b = 0; b < n; ++b) {
-        const int i = id[(size_t)a * n + b];
-        pre[(size_t)(a + 1) * (n + 1) + b + 1] = pre[(size_t)a * (n + 1) + b + 1] + pre[(size_t)(a + 1) * (n + 1) + b] -
-                                                 pre[(size_t)a * (n + 1) + b] + (i >= 0 && row_of[i] < 0);
+  rows.clear();
+  std::vector<int> pending(pairs.size());
+  for (size_t i = 0; i < pairs.size(); ++i) pending[i] = (int)i;
+  while (!pending.empty()) {
+    int a_at[8], b_at[8];
+    for (int k = 0; k < 8; ++k) a_at[k] = b_at[k] = -1;
+    std::vector<int> take, rest;
+    for (int i : pending) {
+      const int a = pairs[i].x, b = pairs[i].y;
+      const bool fit = take.size() < 8 && (a_at[a & 7] < 0 || a_at[a & 7] == a) && (b_at[b & 7] < 0 || b_at[b & 7] == b);
+      if (fit) {
+        a_at[a & 7] = a;
+        b_at[b & 7] = b;
+        take.push_back(i);
+      } else {
+        rest.push_back(i);
       }
-    double best = -1.0;
-    int ba = 0, bb = 0, bwa = 8, bwb = 8;
-    for (const auto& sh : shapes) {
-      const int wa = sh[0], wb = sh[1];
-      const double c = wa / 8 + wb / 8;
-      for (int a0 = 1 - wa; a0 < n; ++a0)
-        for (int b0 = 1 - wb; b0 < n; ++b0) {
-          const double v = std::min(32, cnt(a0, b0, wa, wb)) / c;
-          if (v > best) { best = v; ba = a0; bb = b0; bwa = wa; bwb = wb; }
-        }
     }
-    int lane = 0;
-    for (int a = std::max(ba, 0); a < std::min(n, ba + bwa) && lane < 32; ++a)
-      for (int b = std::max(bb, 0); b < std::min(n, bb + bwb) && lane < 32; ++b) {
-        const int i = id[(size_t)a * n + b];
-        if (i >= 0 && row_of[i] < 0) row_of[i] = groups * 32 + lane++;
-      }
-    left -= (size_t)lane;
-    ++groups;
+    for (int i : take) {
+      row_of[i] = (int)rows.size();
+      rows.push_back(pairs[i]);
+    }
+    const int2 first = pairs[take[0]];
+    while (rows.size() % 8 != 0) rows.push_back(make_int2(-first.x - 1, -first.y - 1));
+    pending.swap(rest);
   }
-  return groups;
+  return (int)rows.size();
 }
 
 // Shell fields of one precision: X, Y, Z passes for every shell.
@@ -592,12 +579,16 @@ bsp_status build_levels(bsp_plan* p, cudaStream_t s) {
     void* tmp = nullptr;
     if (p->prec == BSP_MIXED_BF16X3) {
       L.np = tc_padded_shells(nsh);
-      const int np = (int)pairs.size();
       std::vector<int> row_of;
-      const int groups = assign_tc_rows(pairs, nsh, row_of);
-      L.mtiles = (groups + 3) / 4;
-      std::vector<int2> pab((size_t)std::max(L.mtiles, 1) * 128, make_int2(-1, -1));
-      for (int i = 0; i < np; ++i) pab[row_of[i]] = pairs[i];
+      std::vector<int2> rows;
+      const int nrows = assign_tc_rows(pairs, row_of, rows);
+      L.mtiles = (nrows + 127) / 128;
+      // 8-row phases dealt round-robin over the M tiles, so every tile has the same work
+      const int mt = std::max(L.mtiles, 1);
+      auto place = [mt](int r) { const int ph = r / 8; return (ph % mt) * 128 + (ph / mt) * 8 + r % 8; };
+      std::vector<int2> pab((size_t)mt * 128, make_int2(-1, -1));
+      for (int i = 0; i < nrows; ++i) pab[place(i)] = rows[i];
+      for (int& r : row_of) r = place(r);
       std::vector<int> tmap(L.bins.size());
       int pi = -1;
       for (size_t i = 0; i < L.bins.size(); ++i) {
@@ -609,6 +600,7 @@ bsp_status build_levels(bsp_plan* p, cudaStream_t s) {
       L.vpb = ((chunks + gy - 1) / gy) * kTcVoxelChunk;
       L.gridy = (int)((L.nvox() + L.vpb - 1) / L.vpb);
       if ((st = dev_upload(p, pab, &L.d_tc_pairs, s)) != BSP_OK) return st;
+      L.tc_off = tmap;
       if ((st = dev_upload(p, tmap, &L.d_tc_map, s)) != BSP_OK) return st;
       if ((st = dev_upload(p, L.bins, &L.d_tc_bins, s)) != BSP_OK) return st;
       if ((st = dev_alloc(p, tc_partial_doubles(std::max(L.mtiles, 1), L.gridy, L.np) * sizeof(double), &tmp)) != BSP_OK)
@@ -643,11 +635,25 @@ bsp_status build_levels(bsp_plan* p, cudaStream_t s) {
       if ((st = dev_upload(p, loc, &dloc, s)) != BSP_OK) return st;
       z.loc = dloc;
       z.g = L.g;
+      z.t = L.stride;
       z.rt = 1.0f / (float)L.stride;
       zl.push_back(z);
       zt.push_back(L.stride);
     }
     p->levels.push_back(std::move(L));
+  }
+  if (p->prec == BSP_MIXED_BF16X3) {
+    std::vector<TcBin> tb(p->trips.size());
+    for (const ContractLevel& L : p->levels)
+      for (size_t i = 0; i < L.bins.size(); ++i) {
+        TcBin& b = tb[L.bins[i]];
+        b.partial = L.tc_partial;
+        b.stride = (long long)L.mtiles * 128 * L.np;
+        b.gridy = L.gridy;
+        b.off = L.tc_off[i];
+        b.scale = L.scale;
+      }
+    if ((st = dev_upload(p, tb, &p->d_tc_bins, s)) != BSP_OK) return st;
   }
   if (!zl.empty()) {
     if (zl.size() > 32) return fail(BSP_ERR_NOT_SUPPORTED, "more than 32 contraction levels");
@@ -776,15 +782,9 @@ bsp_status run_contract(bsp_plan* p, const void* fields, double* msum, cudaStrea
   }
   if (mid) BSP_CUDA(cudaEventRecord(mid, s));
   // cross-block sums of every level, scaled to the ng^3 grid
+  if (p->prec == BSP_MIXED_BF16X3) return launch_reduce_tc_all(p->d_tc_bins, (int)p->trips.size(), msum, s);
   for (ContractLevel& L : p->levels) {
-    if (p->prec == BSP_MIXED_BF16X3) {
-      TcArgs a{};
-      a.np = L.np;
-      a.n_mtiles = L.mtiles;
-      a.gridy = L.gridy;
-      a.partial = L.tc_partial;
-      st = launch_reduce_tc(a, L.d_tc_map, L.d_tc_bins, (int)L.bins.size(), msum, L.scale, s);
-    } else {
+    {
       ContractArgs c{};
       c.tile_map = L.d_map;
       c.ntiles = L.ntiles;
@@ -805,9 +805,9 @@ int contract_launches(const bsp_plan* p) {
   for (const ContractLevel& L : p->levels) {
     const bool work = p->prec == BSP_MIXED_BF16X3 ? L.mtiles > 0 : L.ntiles > 0;
     const bool sampled = !L.top && !(p->prec == BSP_MIXED_BF16X3 && p->n_zlev > 0);  // else the Z pass did it
-    n += sampled + 2 * work;
+    n += sampled + (p->prec == BSP_MIXED_BF16X3 ? 1 : 2) * work;
   }
-  return n;
+  return n + (p->prec == BSP_MIXED_BF16X3 ? 1 : 0);  // one cross-block sum for all tensor-core levels
 }
 
 // The three pass launches of an estimate on the plan's buffers; ev (optional) receives an event

@@ -3,22 +3,28 @@
 // The numerator of Eq. (2.7) for every kept bin is read off one dense contraction
 //     M[(a,b), c] = sum_x P_ab(x) d_c(x),    P_ab = d_a d_b,
 // a GEMM with M = pairs (128 per tile), N = shells (padded to NP), K = voxels. Both operands are
-// split into bf16 high and low parts, P = Ph + Pl and d = dh + dl, and three MMAs per K step
-// accumulate Ph dh + Ph dl + Pl dh in FP32 (relative error about 2^-16 per product).
+// split into bf16 high and low parts, P = Ph + Pl and d = dh + dl, and the MMAs accumulate
+// (Ph + Pl)(dh + dl) in FP32 (relative error about 2^-16 per product). With NP = 32 the high and
+// low rows of the fields form one N = 64 operand [dh | dl]: two MMAs per K step (Ph and Pl) fill
+// two 32-column halves whose sum is the result; an N = 32 MMA costs about as long as an N = 64
+// one, so this is a third fewer MMA instructions. With NP = 64 three MMAs per K step accumulate
+// Ph dh + Ph dl + Pl dh.
 //
 // The fields arrive already split (two bf16 planes, written so by the Z pass). Per block (one per
 // SM, one M tile of 128 pair rows, a contiguous voxel range), warp roles:
-//   * loader warp: per 128-voxel chunk, four tiled TMA loads (high and low plane, two 64-voxel
-//     boxes each) bring the chunk's fields, NP shell rows of 128 bytes with the 128-byte swizzle,
-//     into an NB-stage shared-memory ring; they complete on the stage's "full" mbarrier. The
-//     same bytes are the B operand of the MMAs: no copy or conversion in the block.
+//   * loader warp: per 128-voxel chunk, four tiled TMA loads (two 64-voxel halves, high and low
+//     plane each) bring the chunk's fields, NP shell rows of 128 bytes with the 128-byte swizzle,
+//     into an NB-stage shared-memory ring, laid out [half][plane][row]; they complete on the
+//     stage's "full" mbarrier. The same bytes are the B operand of the MMAs.
 //   * 16 generator warps (4 per TMEM lane quarter, 32 voxels each): every thread owns one pair
 //     row (its TMEM lane). It forms the pair products from the split fields in shared memory
 //     (bf16x2 arithmetic, two voxels per instruction) and writes the A operand straight into
-//     tensor memory with tcgen05.st. A lane quarter with no pair row does no work.
-//   * MMA warp: one thread issues 24 MMAs per chunk (8 K steps x 3 products) into an FP32
-//     accumulator in tensor memory and commits them to the B stage's "mma done" mbarrier, which
-//     frees the B stage for the loader and (NA chunks later) the A stage for the generators.
+//     tensor memory with tcgen05.st. A lane quarter with no pair row does no work. A warp forms
+//     chunk i's products first and only then waits for the MMAs of chunk i - NA to free its A
+//     stage, so the products overlap those MMAs.
+//   * MMA warp: one thread issues the MMAs of a chunk (8 K steps) into an FP32 accumulator in
+//     tensor memory and commits them to the B stage's "mma done" mbarrier, which frees the B
+//     stage for the loader and (NA chunks later) the A stage for the generators.
 //   A lives in a 3-stage tensor-memory ring, B in the shared-memory ring, so loads, generation
 //   and MMAs of consecutive chunks overlap; warps hand stages over through mbarriers only.
 //   Every 32 chunks (4096 voxels) the generators read the accumulator back (tcgen05.ld) into FP64
@@ -48,9 +54,12 @@ static_assert(kTcChunk == 2 * kTcBox, "two boxes per chunk");
 template <int NP>
 struct TcSmem {
   static constexpr int kNB = NP == 32 ? 8 : 6;     // B stages (shared memory)
-  static constexpr int kBHalf = NP * 128;          // one box: NP rows x 128 bytes
-  static constexpr int kBPart = 2 * kBHalf;        // one bf16 plane of a chunk
-  static constexpr int kBStage = 2 * kBPart;       // high and low planes
+  static constexpr int kBHalf = NP * 128;          // one box: NP rows x 128 bytes (one plane)
+  static constexpr int kBPart = kBHalf;            // high -> low plane of a half
+  static constexpr int kBHalfStride = 2 * kBHalf;  // 64-voxel half -> next half
+  static constexpr int kBStage = 2 * kBHalfStride; // two halves
+  static constexpr bool kJoint = NP == 32;         // [dh | dl] as one N = 64 operand
+  static constexpr int kDN = kJoint ? 2 * NP : NP; // accumulator columns of one run
   static constexpr int kBarOff = kNB * kBStage;
   // barriers: full[NB], mmad[NB], gen[NA], drain; then the TMEM slot and the abort flag
   static constexpr int kNumBars = 2 * kNB + kTcNA + 1;
@@ -118,10 +127,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   ptx::tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   // TMEM columns: A stage s at [128 s, 128 s + 128) (hi +0..63, lo +64..127), s < 3;
-  // FP32 accumulators of run parity r at [384 + NP r, 384 + NP (r + 1)).
+  // FP32 accumulators of run parity r at [384 + DN r, 384 + DN (r + 1)).
   constexpr uint32_t kAcols = kTcChunk;  // 32-bit columns of one A stage (hi and lo halves)
   constexpr uint32_t kDcol = kAcols * kTcNA;
-  static_assert(kDcol + 2 * NP <= kTcCols, "tensor memory budget");
+  static_assert(kDcol + 2 * L::kDN <= kTcCols, "tensor memory budget");
   bool failed = false;
 
   if (warp == kTcGenWarps) {
@@ -142,13 +151,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         for (int part = 0; part < 2; ++part)
 #pragma unroll
           for (int h = 0; h < 2; ++h)
-            ptx::tma_load_3d(dst + part * L::kBPart + h * L::kBHalf, &tmap, x + kTcBox * h, 0, part, &full[s]);
+            ptx::tma_load_3d(dst + h * L::kBHalfStride + part * L::kBPart, &tmap, x + kTcBox * h, 0, part, &full[s]);
       }
       __syncwarp();
     }
   } else if (warp == kTcGenWarps + 1) {
     // ------------------------------------------------------------ MMA issuer
-    constexpr uint32_t idesc = ptx::idesc_bf16_f32(128, NP);
+    constexpr uint32_t idesc = ptx::idesc_bf16_f32(128, L::kDN);
     for (int i = 0; i < nchunks; ++i) {
       const int sa = i % kTcNA;
       const int sb = i % L::kNB;
@@ -161,19 +170,23 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       if (lane == 0) {
         const int run = i / kTcRun;
         const bool first = (i % kTcRun) == 0;
-        const uint32_t dcol = tmem + kDcol + (uint32_t)(NP * (run & 1));
+        const uint32_t dcol = tmem + kDcol + (uint32_t)(L::kDN * (run & 1));
         const uint32_t b0 = ptx::smem_u32(bs + (size_t)sb * L::kBStage);
 #pragma unroll
         for (int ks = 0; ks < kTcChunk / 16; ++ks) {
           const uint32_t ahi = tmem + (uint32_t)(kAcols * sa + 8 * ks);
           const uint32_t alo = ahi + kAcols / 2;
-          // K step ks: box ks / 4, 32-byte column step ks % 4 inside the swizzle atom
-          const uint32_t off = (uint32_t)((ks >> 2) * L::kBHalf + (ks & 3) * 32);
-          const uint64_t dh = ptx::smem_desc_sw128(b0 + off, 1024u);
-          const uint64_t dl = ptx::smem_desc_sw128(b0 + L::kBPart + off, 1024u);
+          // K step ks: half ks / 4, 32-byte column step ks % 4 inside the swizzle atom
+          const uint32_t off = (uint32_t)((ks >> 2) * L::kBHalfStride + (ks & 3) * 32);
+          const uint64_t dh = ptx::smem_desc_sw128(b0 + off, 1024u);  // with kJoint: rows dh then dl
           ptx::mma_bf16_ts(dcol, ahi, dh, idesc, (first && ks == 0) ? 0u : 1u);
-          ptx::mma_bf16_ts(dcol, ahi, dl, idesc, 1u);
-          ptx::mma_bf16_ts(dcol, alo, dh, idesc, 1u);
+          if constexpr (L::kJoint) {
+            ptx::mma_bf16_ts(dcol, alo, dh, idesc, 1u);
+          } else {
+            const uint64_t dl = ptx::smem_desc_sw128(b0 + off + L::kBPart, 1024u);
+            ptx::mma_bf16_ts(dcol, ahi, dl, idesc, 1u);
+            ptx::mma_bf16_ts(dcol, alo, dh, idesc, 1u);
+          }
         }
         ptx::mma_commit(&mmad[sb]);
       }
@@ -189,23 +202,27 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const uint32_t lane_base = (uint32_t)(32 * quarter) << 16;
     const int2 ab = a.pair_ab[mtile * 128 + row];
     const bool active = __any_sync(0xffffffffu, ab.x >= 0);
-    // padding rows of an active quarter compute d_0^2: their accumulator rows are never read
-    // (a D row depends only on its own A row)
-    const int ra = ab.x >= 0 ? ab.x : 0;
-    const int rb = ab.x >= 0 ? ab.y : 0;
+    // padding rows hold (-a - 1, -b - 1) of a real row of their 8-row phase (a broadcast read);
+    // their accumulator rows are never read (a D row depends only on its own A row)
+    const int ra = ab.x >= 0 ? ab.x : -ab.x - 1;
+    const int rb = ab.x >= 0 ? ab.y : -ab.y - 1;
     constexpr int kCols = NP / 4;  // accumulator columns this thread flushes
     double acc[kCols];
 #pragma unroll
     for (int j = 0; j < kCols; ++j) acc[j] = 0.0;
     auto flush = [&](int run) {
-      const uint32_t dcol = kDcol + (uint32_t)(NP * (run & 1)) + (uint32_t)(kCols * sub);
+      const uint32_t dcol = kDcol + (uint32_t)(L::kDN * (run & 1)) + (uint32_t)(kCols * sub);
 #pragma unroll
       for (int j0 = 0; j0 < kCols; j0 += 8) {
-        uint32_t v[8];
+        uint32_t v[8], w[8];
         ptx::tmem_ld8(tmem + lane_base + dcol + j0, v);
+        if constexpr (L::kJoint) ptx::tmem_ld8(tmem + lane_base + dcol + NP + j0, w);  // the dl half
         ptx::tmem_ld_wait();
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[j0 + j] += (double)__uint_as_float(v[j]);
+        for (int j = 0; j < 8; ++j) {
+          acc[j0 + j] += (double)__uint_as_float(v[j]);
+          if constexpr (L::kJoint) acc[j0 + j] += (double)__uint_as_float(w[j]);
+        }
       }
     };
     // Hand a finished A stage to the MMA warp once its tensor-memory stores have landed. Done one
@@ -216,32 +233,21 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       __syncwarp();
       if (lane == 0) ptx::mbar_arrive(&gen[s]);
     };
-    // Field n, voxels [32 sub + 8 m, +8) of a plane: row n of box sub / 2 (8-row atoms of 1024
+    // Field n, voxels [32 sub + 8 m, +8) of a plane: row n of half sub / 2 (8-row atoms of 1024
     // bytes, 128-byte rows), 16-byte column (4 (sub & 1) + m) XOR (n & 7) (the TMA's swizzle).
     const int half = sub >> 1;
     const int j0 = (sub & 1) * 4;
-    const int rowa = half * L::kBHalf + (ra >> 3) * 1024 + (ra & 7) * 128;
-    const int rowb = half * L::kBHalf + (rb >> 3) * 1024 + (rb & 7) * 128;
+    const int rowa = half * L::kBHalfStride + (ra >> 3) * 1024 + (ra & 7) * 128;
+    const int rowb = half * L::kBHalfStride + (rb >> 3) * 1024 + (rb & 7) * 128;
     const int xa = ra & 7, xb = rb & 7;
     for (int i = 0; active && i < nchunks; ++i) {
       const int sa = i % kTcNA;
       const int sb = i % L::kNB;
-      bool ok = tc_wait(&full[sb], (uint32_t)((i / L::kNB) & 1), abort_flag);
-      if (ok && i >= kTcNA) {
-        const int j = i - kTcNA;  // the chunk that last used A stage sa
-        ok = tc_wait(&mmad[j % L::kNB], (uint32_t)((j / L::kNB) & 1), abort_flag);
-      }
-      if (!ok) {
+      if (!tc_wait(&full[sb], (uint32_t)((i / L::kNB) & 1), abort_flag)) {
         *abort_flag = 1;
         failed = true;
         break;
       }
-      ptx::tc_fence_after();
-      // The MMAs of chunk i - NA, the first chunk of run r, have completed, and with them every
-      // MMA of run r - 1 (MMAs complete in issue order): read that run's accumulator now. Its
-      // columns are next written by run r + 1, which starts only after chunk (r + 1) * RUN has
-      // been generated, later in this loop.
-      if (i >= kTcRun && i % kTcRun == kTcNA) flush(i / kTcRun - 1);
       const unsigned char* st = bs + (size_t)sb * L::kBStage;
       // A operand: 32 pair products of this row from the split fields a and b
       uint32_t hv[16], lv[16];
@@ -259,6 +265,20 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         ptx::bf16x2_pair_product(ah.w, al.w, bh.w, bl.w, hv[4 * m + 3], lv[4 * m + 3]);
       }
       if (i > 0) publish((i - 1) % kTcNA);
+      if (i >= kTcNA) {
+        const int j = i - kTcNA;  // the chunk that last used A stage sa
+        if (!tc_wait(&mmad[j % L::kNB], (uint32_t)((j / L::kNB) & 1), abort_flag)) {
+          *abort_flag = 1;
+          failed = true;
+          break;
+        }
+      }
+      ptx::tc_fence_after();
+      // The MMAs of chunk i - NA, the first chunk of run r, have completed, and with them every
+      // MMA of run r - 1 (MMAs complete in issue order): read that run's accumulator now. Its
+      // columns are next written by run r + 1, which starts only after chunk (r + 1) * RUN has
+      // been generated, later in this loop.
+      if (i >= kTcRun && i % kTcRun == kTcNA) flush(i / kTcRun - 1);
       const uint32_t acol = (uint32_t)(kAcols * sa + 16 * sub);
       ptx::tmem_st16(tmem + lane_base + acol, hv);
       ptx::tmem_st16(tmem + lane_base + acol + kAcols / 2, lv);
@@ -319,7 +339,29 @@ __global__ void reduce_tc_kernel(const double* partial, int gridy, long long str
   msum[bins ? bins[t] : t] = scale * s;
 }
 
+// msum[t] for the bins of all levels: lane l adds blocks y = l, l + 32, ... in order, then the
+// warp adds its 32 partial sums by a fixed butterfly, so the result does not depend on timing.
+__global__ void reduce_tc_all_kernel(const TcBin* __restrict__ bins, int n, double* __restrict__ msum) {
+  const int t = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (t >= n) return;
+  const TcBin b = bins[t];
+  double s = 0.0;
+  for (int y = lane; y < b.gridy; y += 32) s += b.partial[(long long)y * b.stride + b.off];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) msum[t] = b.scale * s;
+}
+
 }  // namespace
+
+bsp_status launch_reduce_tc_all(const TcBin* bins, int n, double* msum, cudaStream_t s) {
+  if (n == 0) return BSP_OK;
+  const long long threads = 32LL * n;
+  reduce_tc_all_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(bins, n, msum);
+  BSP_CUDA(cudaGetLastError());
+  return BSP_OK;
+}
 
 int tc_padded_shells(int ns) { return ns <= 32 ? 32 : 64; }
 

@@ -28,27 +28,31 @@ constexpr int kLines = 8;           // lines per X/Y block
 constexpr int kZThreads = 256;      // 8 warps, one line at a time each
 constexpr int kTileLd = kLines + 1; // padded tile row (complex)
 
-// Padding of the per-line exchange buffers: one spare slot every 16 points for power-of-two
-// lengths (their stage strides are powers of two), none for 3 * 2^p lengths (strides that are
-// multiples of 3 already spread over the banks). Chosen by counting shared-memory wavefronts of
-// every stage's load and store pattern.
-template <int N> struct Pad { static constexpr int shift = (N % 3 == 0) ? 0 : (N == 64 ? 2 : 4); };
+// Padding of the per-line exchange buffers: one spare slot every 2^shift points. Chosen per
+// length and radix list by counting the shared-memory wavefronts of every stage's load and store
+// pattern (64-bit accesses, two half-warp phases): 4 for most lengths, 2 for 64, 5 for 384, none
+// for 96.
+template <int N> struct Pad { static constexpr int shift = N == 96 ? 0 : (N == 64 ? 2 : (N == 384 ? 5 : 4)); };
 template <int N> __device__ __forceinline__ int padn(int i) {
   return Pad<N>::shift ? i + (i >> Pad<N>::shift) : i;
 }
 template <int N> __host__ __device__ constexpr int pad_len() { return Pad<N>::shift ? N + (N >> Pad<N>::shift) : N; }
+// Line stride of the X/Y buffers: 2 mod 16 complex, so the transposed read-out (8 lines x 2
+// consecutive points per half-warp) hits 16 distinct bank pairs.
+template <int N> __host__ __device__ constexpr int line_ld() { return pad_len<N>() + ((18 - pad_len<N>() % 16) % 16); }
 
 // Radix list and lanes per line of each supported length: every radix divides the points per
-// lane E = N / LPL, so each lane runs E / R whole butterflies per stage.
+// lane E = N / LPL, so each lane runs E / R whole butterflies per stage. Lengths 3 * 2^p use the
+// radix-6 and radix-12 butterflies: one exchange fewer than radix 3 followed by radices 2 to 4.
 template <int N> struct Radices;
 template <> struct Radices<64> { static constexpr int lpl = 16, n = 3; static constexpr int r[3] = {4, 4, 4}; };
-template <> struct Radices<96> { static constexpr int lpl = 8, n = 4; static constexpr int r[4] = {3, 4, 4, 2}; };
+template <> struct Radices<96> { static constexpr int lpl = 8, n = 3; static constexpr int r[3] = {6, 4, 4}; };
 template <> struct Radices<128> { static constexpr int lpl = 32, n = 4; static constexpr int r[4] = {4, 4, 4, 2}; };
-template <> struct Radices<192> { static constexpr int lpl = 16, n = 4; static constexpr int r[4] = {3, 4, 4, 4}; };
+template <> struct Radices<192> { static constexpr int lpl = 16, n = 3; static constexpr int r[3] = {4, 12, 4}; };
 template <> struct Radices<256> { static constexpr int lpl = 32, n = 3; static constexpr int r[3] = {8, 8, 4}; };
-template <> struct Radices<384> { static constexpr int lpl = 32, n = 5; static constexpr int r[5] = {3, 4, 4, 4, 2}; };
+template <> struct Radices<384> { static constexpr int lpl = 32, n = 4; static constexpr int r[4] = {12, 4, 4, 2}; };
 template <> struct Radices<512> { static constexpr int lpl = 32, n = 3; static constexpr int r[3] = {8, 8, 8}; };
-template <> struct Radices<768> { static constexpr int lpl = 32, n = 4; static constexpr int r[4] = {3, 8, 8, 4}; };
+template <> struct Radices<768> { static constexpr int lpl = 32, n = 3; static constexpr int r[3] = {8, 8, 12}; };
 template <> struct Radices<1024> { static constexpr int lpl = 32, n = 4; static constexpr int r[4] = {8, 8, 8, 2}; };
 
 // Offset of stage S's twiddles in the stage-ordered table of length N: stage s (sub-transforms of
@@ -140,7 +144,7 @@ __global__ void __launch_bounds__(XY<N>::kThreads) xy_warp_kernel(PassArgs a) {
   constexpr int LPL = XY<N>::kLpl;
   constexpr int NT = XY<N>::kThreads;
   constexpr int E = N / LPL;
-  constexpr int kBufLd = pad_len<N>();
+  constexpr int kBufLd = line_ld<N>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* tw = reinterpret_cast<float2*>(smem_raw);  // N entries exp(2 pi i t / N)
   float2* bufs = tw + N;                               // kLines x kBufLd
@@ -320,27 +324,26 @@ __global__ void __launch_bounds__(kZThreads, 4) z_warp_kernel(PassArgs a, long l
           const ZLevel L = a.zlev[l];
           const int j = L.loc[n];
           if (j < 0) continue;
-          const uint32_t bit = 1u << l;
           uint16_t* lh = L.dst + (((long long)j * L.g + __float2int_rn(x * L.rt)) * L.g + __float2int_rn(y * L.rt)) * L.g;
 #pragma unroll
           for (int b = 0; b < BPLL; ++b)
 #pragma unroll
             for (int rr = 0; rr < RL; ++rr) {
               const int k = lane + b * LPL + rr * (M / RL);
-              const bool e0 = (zmask[2 * k] & bit) != 0, e1 = (zmask[2 * k + 1] & bit) != 0;
+              // z = 2k and 2k + 1 on the level's grid: z / t by the rounded reciprocal, kept when exact
+              const int q0 = __float2int_rn((2 * k) * L.rt), q1 = __float2int_rn((2 * k + 1) * L.rt);
+              const bool e0 = q0 * L.t == 2 * k, e1 = q1 * L.t == 2 * k + 1;
               if (e0 || e1) {
                 const float2 x2 = v[b * RL + rr];
                 uint32_t h, lo;
                 ptx::split_bf16x2(ptx::f2_pack(x2.x, x2.y), h, lo);
                 if (e0) {
-                  const int zz = __float2int_rn((2 * k) * L.rt);
-                  lh[zz] = (uint16_t)(h & 0xFFFFu);
-                  lh[L.lo_off + zz] = (uint16_t)(lo & 0xFFFFu);
+                  lh[q0] = (uint16_t)(h & 0xFFFFu);
+                  lh[L.lo_off + q0] = (uint16_t)(lo & 0xFFFFu);
                 }
                 if (e1) {
-                  const int zz = __float2int_rn((2 * k + 1) * L.rt);
-                  lh[zz] = (uint16_t)(h >> 16);
-                  lh[L.lo_off + zz] = (uint16_t)(lo >> 16);
+                  lh[q1] = (uint16_t)(h >> 16);
+                  lh[L.lo_off + q1] = (uint16_t)(lo >> 16);
                 }
               }
             }
@@ -411,7 +414,7 @@ __global__ void __launch_bounds__(XY<N>::kThreads) xyf_warp_kernel(PassArgs a, f
   constexpr int LPL = XY<N>::kLpl;
   constexpr int NT = XY<N>::kThreads;
   constexpr int E = N / LPL;
-  constexpr int kBufLd = pad_len<N>();
+  constexpr int kBufLd = line_ld<N>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* tw = reinterpret_cast<float2*>(smem_raw);  // N
   float2* bufs = tw + N;                               // kLines x kBufLd
@@ -494,7 +497,7 @@ __global__ void __launch_bounds__(XY<N>::kThreads) xyf_warp_kernel(PassArgs a, f
 template <int N, bool XPASS>
 bsp_status launch_xyf(const PassArgs& a, int n_items, float scale, cudaStream_t s) {
   if (n_items == 0) return BSP_OK;
-  const size_t smem = ((size_t)N + (size_t)kLines * pad_len<N>() + (size_t)N * kTileLd) * sizeof(float2);
+  const size_t smem = ((size_t)N + (size_t)kLines * line_ld<N>() + (size_t)N * kTileLd) * sizeof(float2);
   BSP_CUDA(cudaFuncSetAttribute(xyf_warp_kernel<N, XPASS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   xyf_warp_kernel<N, XPASS><<<n_items, XY<N>::kThreads, smem, s>>>(a, scale);
   BSP_CUDA(cudaGetLastError());
@@ -522,7 +525,7 @@ bsp_status launch_xy(const PassArgs& a, int n_items, cudaStream_t s) {
   if (n_items == 0) return BSP_OK;
   // the tile holds 2 r - 1 rows of the largest shell
   const size_t smem =
-      ((size_t)N + (size_t)kLines * pad_len<N>() + (size_t)(2 * a.rmax) * kTileLd) * sizeof(float2);
+      ((size_t)N + (size_t)kLines * line_ld<N>() + (size_t)(2 * a.rmax) * kTileLd) * sizeof(float2);
   BSP_CUDA(cudaFuncSetAttribute(xy_warp_kernel<N, XPASS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   xy_warp_kernel<N, XPASS><<<n_items, XY<N>::kThreads, smem, s>>>(a);
   BSP_CUDA(cudaGetLastError());

@@ -90,7 +90,8 @@ struct ZLevel {
   long long lo_off;   // nsh * g^3: offset of the low plane (elements)
   const int* loc;     // [ns]: the level's field index of each shell, -1 if unused
   int g;              // level side
-  float rt;           // 1 / t (t divides every coordinate it is applied to: exact after rounding)
+  int t;              // stride: evaluation-grid side / g
+  float rt;           // 1 / t (x / t = rint(x rt) for the multiples x of t below 2^24)
 };
 
 // Warp-per-line FP32 passes (bispec_fft_warp.cu) for evaluation grids 2^p and 3 * 2^p from
@@ -197,6 +198,16 @@ bsp_status launch_split_fields(const float* src, uint32_t* dst, long long n_word
 // (bins may be null: identity)
 bsp_status launch_reduce_tc(const TcArgs& a, const int* map, const int* bins, int n_out, double* msum,
                             double scale, cudaStream_t s);
+// One kept bin of the tensor-core contraction: msum[t] = scale * sum_y partial[y * stride + off].
+struct TcBin {
+  const double* partial;
+  long long stride;
+  int gridy;
+  int off;
+  double scale;
+};
+// Every bin of every level in one launch (one warp per bin, a fixed summation order).
+bsp_status launch_reduce_tc_all(const TcBin* bins, int n, double* msum, cudaStream_t s);
 
 // ---------------------------------------------------------------- gradient (bispec_grad.cu)
 bsp_status launch_build_w(const double* g, const double* cnorm, const int* ptr, const int* idx, int n_entries,
