@@ -28,12 +28,16 @@ constexpr int kLines = 8;           // lines per X/Y block
 constexpr int kZThreads = 256;      // 8 warps, one line at a time each
 constexpr int kTileLd = kLines + 1; // padded tile row (complex)
 
-// Padding of the per-line exchange buffers: one spare slot every 2^shift points. Chosen per
-// length and radix list by counting the shared-memory wavefronts of every stage's load and store
-// pattern (64-bit accesses, two half-warp phases): 4 for most lengths, 2 for 64, 5 for 384, none
-// for 96.
-template <int N> struct Pad { static constexpr int shift = N == 96 ? 0 : (N == 64 ? 2 : (N == 384 ? 5 : 4)); };
+// Placement of point i in the per-line exchange buffers, chosen per length and radix list by
+// counting the shared-memory wavefronts of every stage's load and store pattern (64-bit accesses,
+// two half-warp phases): length 384 permutes i by i XOR ((i >> 4) & 3) (no extra space), 96 is
+// unpadded, the others get one spare slot every 2^shift points (shift 2 for 64, else 4).
+template <int N> struct Pad {
+  static constexpr bool kXor = N == 384;
+  static constexpr int shift = (kXor || N == 96) ? 0 : (N == 64 ? 2 : 4);
+};
 template <int N> __device__ __forceinline__ int padn(int i) {
+  if constexpr (Pad<N>::kXor) return i ^ ((i >> 4) & 3);
   return Pad<N>::shift ? i + (i >> Pad<N>::shift) : i;
 }
 template <int N> __host__ __device__ constexpr int pad_len() { return Pad<N>::shift ? N + (N >> Pad<N>::shift) : N; }
@@ -69,9 +73,21 @@ __host__ __device__ constexpr int stage_off(int S) {
   return off;
 }
 
+// w^2 .. w^(R-1) from w by squarings and one multiplication per odd power (at most about
+// 2 log2 R products deep): p[r - 1] = w^r.
+template <int R>
+__device__ __forceinline__ void twiddle_powers(float2 w, float2* p) {
+  p[0] = w;
+#pragma unroll
+  for (int r = 2; r < R; ++r) p[r - 1] = (r % 2 == 0) ? c_mul(p[r / 2 - 1], p[r / 2 - 1]) : c_mul(p[r - 2], w);
+}
+
 // One Stockham stage of radix R after sub-transforms of length NS; v[b R + r] is input r of
-// butterfly j = lane + b LPL; stw is the stage-ordered twiddle table.
-template <int N, int LPL, int R, int NS, int OFF>
+// butterfly j = lane + b LPL; stw is the stage-ordered twiddle table. POW: read only the first
+// twiddle of each butterfly, exp(2 pi i k / (NS R)), and form the others as its powers (less
+// shared-memory traffic, more arithmetic: the X/Y passes, which are bound by the former);
+// otherwise read all R - 1 (the Z pass, whose arithmetic is the tighter limit).
+template <int N, int LPL, int R, int NS, int OFF, bool POW>
 __device__ __forceinline__ void stage_compute(float2* v, int lane, const float2* stw) {
   constexpr int BPL = N / (R * LPL);
 #pragma unroll
@@ -79,8 +95,15 @@ __device__ __forceinline__ void stage_compute(float2* v, int lane, const float2*
     const int j = lane + b * LPL;
     const int k = j % NS;
     if (NS > 1) {
+      if constexpr (POW) {
+        float2 w[R - 1];
+        twiddle_powers<R>(stw[OFF + k * (R - 1)], w);
 #pragma unroll
-      for (int r = 1; r < R; ++r) v[b * R + r] = c_mul(v[b * R + r], stw[OFF + k * (R - 1) + (r - 1)]);
+        for (int r = 1; r < R; ++r) v[b * R + r] = c_mul(v[b * R + r], w[r - 1]);
+      } else {
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[b * R + r] = c_mul(v[b * R + r], stw[OFF + k * (R - 1) + (r - 1)]);
+      }
     }
     Dft<float2, R>::run(v + b * R);
   }
@@ -112,17 +135,17 @@ __device__ __forceinline__ void stage_load(const float2* buf, float2* v, int lan
 
 // Inverse FFT of one line held by LPL lanes: on entry v[b R1 + r] = x[lane + b LPL + r N/R1],
 // on exit v[b RL + r] = y[lane + b LPL + r N/RL] (R1, RL the first and last radices).
-template <int N, int LPL, int S, int NS>
+template <int N, int LPL, int S, int NS, bool POW = true>
 __device__ __forceinline__ void warp_fft_from(float2* v, float2* buf, int lane, const float2* stw) {
   constexpr int R = Radices<N>::r[S];
-  stage_compute<N, LPL, R, NS, stage_off<N>(S)>(v, lane, stw);
+  stage_compute<N, LPL, R, NS, stage_off<N>(S), POW>(v, lane, stw);
   if constexpr (S + 1 < Radices<N>::n) {
     constexpr int R2 = Radices<N>::r[S + 1];
     __syncwarp();
     stage_store<N, LPL, R, NS>(buf, v, lane);
     __syncwarp();
     stage_load<N, LPL, R2>(buf, v, lane);
-    warp_fft_from<N, LPL, S + 1, NS * R>(v, buf, lane, stw);
+    warp_fft_from<N, LPL, S + 1, NS * R, POW>(v, buf, lane, stw);
   }
 }
 
@@ -239,8 +262,6 @@ __global__ void __launch_bounds__(XY<N>::kThreads) xy_warp_kernel(PassArgs a) {
 }
 
 // ---------------------------------------------------------------- Z pass
-// Lines (shell n, x, y) of the S^3 evaluation grid in order; each group of LPL lanes takes
-// lines id, id + groups, ...
 template <int S>
 __global__ void __launch_bounds__(kZThreads, 4) z_warp_kernel(PassArgs a, long long n_lines) {
   constexpr int M = S / 2;
@@ -290,7 +311,7 @@ __global__ void __launch_bounds__(kZThreads, 4) z_warp_kernel(PassArgs a, long l
         const float2 o = c_mul(make_float2(xk.x - xm.x, xk.y + xm.y), wk[k]);  // (X[k] - conj X[M-k]) W^k
         v[b * R1 + rr] = make_float2(e.x - o.y, e.y + o.x);                    // e + i o
       }
-    warp_fft_from<M, LPL, 0, 1>(v, buf, lane, tw);
+    warp_fft_from<M, LPL, 0, 1, false>(v, buf, lane, tw);
     const long long off = (long long)n * S * plane + xy * S;  // first voxel of the line
     if (a.split_lo == 0) {
       float2* dst = reinterpret_cast<float2*>(static_cast<float*>(a.fields) + off);
