@@ -227,7 +227,8 @@ def metric_name(w):
 def config_of(w, precision):
     return {"workload": w["text"], "ng": w["ng"], "box_len": w["box"], "n_shells": w["ns"],
             "n_mu": w["n_mu"], "n_t": w["n_t"], "rsd_beta": w["beta"], "precision": precision,
-            "l2": "inputs larger than L2 (spectrum 0.54 GB, shell fields >16 GB per step)"}
+            "l2": "no flush: every step streams its spectrum, FFT intermediates and shell fields, all larger "
+                  "than the 129 MB L2"}
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -248,7 +249,8 @@ def run_ours(args, w):
     spec = torch.from_numpy(spec_np).cuda()
     t0 = time.perf_counter()
     plan = binding.Plan(w["ng"], w["box"], edges_of(w), w["n_mu"], w["n_t"],
-                        rsd=w["beta"] is not None, beta=w["beta"] or 0.0, precision=args.precision)
+                        rsd=w["beta"] is not None, beta=w["beta"] or 0.0, precision=args.precision,
+                        autotune=not args.no_autotune)
     plan_s = time.perf_counter() - t0
     log(f"[bench] plan: {plan.n_triplets} bins, {plan.device_bytes / 1e9:.1f} GB on device, "
         f"{plan_s:.1f} s")
@@ -385,7 +387,7 @@ def run_ours(args, w):
             "fields_per_sec": fields_per_s, "n_bins": plan.n_triplets, "roofline": roof,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(nlaunch.value), "clocks": clk,
             "stages": stages, "plan_seconds": round(plan_s, 2), "plain_fp32": plain,
-            "eval_grid": plan.ng_eval}
+            "eval_grid": plan.ng_eval, "contraction_levels": plan.tuning}
     if rank == 0:
         print(json.dumps(line), flush=True)
     plan.close()
@@ -403,7 +405,7 @@ def run_batch(args, w):
     plans, specs, nbytes = [], [], 0
     for ng, count in w["grids"]:
         plan = binding.Plan(ng, float(ng), np.linspace(1.0, ng / 4, w["ns"] + 1), w["n_mu"], w["n_t"],
-                            precision=args.precision)
+                            precision=args.precision, autotune=not args.no_autotune)
         for i in range(count):
             sp = fieldgen.half_spectrum_c64(fieldgen.quadratic_field(ng, float(ng), 1.5, 0.05, 100 + len(specs)))
             nbytes += sp.nbytes
@@ -458,6 +460,8 @@ def main():
                     help="skip timing the plain FP32 (CUDA-core contraction) form beside the main one")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="ng512_rsd")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="plans skip the contraction autotuner (fixed split: one voxel block per SM)")
     args = ap.parse_args()
     if args.warmup < 3:
         log("[bench] warmup raised to 3")

@@ -74,6 +74,10 @@ typedef struct {
   double beta;             /* linear RSD parameter beta_1 of Eq. (3.4) */
   int precision;           /* a bsp_precision */
   size_t mem_budget_bytes; /* reserved, 0 */
+  int autotune;            /* 1: at creation, time the tensor-core contraction of every level with
+                              its voxels split over 1, 2 and 4 x (SM count) blocks per M tile and
+                              keep the fastest (BSP_MIXED_BF16X3 plans; the split changes only the
+                              order of the FP64 cross-block sums). No counterpart in the paper. */
 } bsp_plan_desc;
 
 /* One bin of triangles (Sec. 2.1): shells a >= b >= c and their labels (Eq. (2.4)). */
@@ -105,6 +109,13 @@ BSP_API bsp_status bsp_plan_destroy(bsp_plan* plan);
 /* Sizes of a plan: kept bins, shells, bytes of one shell-field set, device bytes held. */
 BSP_API bsp_status bsp_plan_info(const bsp_plan* plan, int* n_triplets, int* n_shells,
                          size_t* field_bytes, size_t* device_bytes);
+
+/* The contraction levels of a plan (no counterpart in the paper): for level l < *n_levels
+ * (ascending side), level_side[l] = its grid side g and blocks_mult[l] = the voxel blocks per M
+ * tile divided by the SM count (the autotuner's choice; 1 without it; 0 for a level on the CUDA
+ * cores). Arrays: host, at least max_levels entries each, may be NULL. */
+BSP_API bsp_status bsp_plan_tuning(const bsp_plan* plan, int* n_levels, int* level_side, int* blocks_mult,
+                                   int max_levels);
 
 /* Side of the plan's evaluation grid, ng_eval <= ng. Every shell mode has |m_i| <= r - 1, so a
  * triple product of shell fields only holds wavevectors with |k_i| <= 3 (r - 1); summed over any

@@ -22,7 +22,7 @@ class PlanDesc(C.Structure):
     _fields_ = [("ng", C.c_int), ("box_len", C.c_double), ("n_shells", C.c_int),
                 ("edges_kf", C.POINTER(C.c_double)), ("n_mu", C.c_int), ("n_t", C.c_int),
                 ("rsd", C.c_int), ("beta", C.c_double), ("precision", C.c_int),
-                ("mem_budget_bytes", C.c_size_t)]
+                ("mem_budget_bytes", C.c_size_t), ("autotune", C.c_int)]
 
 
 class Triplet(C.Structure):
@@ -44,6 +44,7 @@ SIGNATURES = {
     "bsp_plan_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                 C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]),
     "bsp_plan_grid": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
+    "bsp_plan_tuning": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_int]),
     "bsp_plan_triplets": (C.c_int, [C.c_void_p, C.POINTER(C.POINTER(Triplet)), C.POINTER(C.c_int)]),
     "bsp_shell_fields": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "bsp_contract": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),

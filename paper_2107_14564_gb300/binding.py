@@ -52,6 +52,16 @@ def bsp_plan_grid(handle) -> int:
     return n.value
 
 
+def bsp_plan_tuning(handle):
+    """[(level side g, blocks per M tile / SM count)] in ascending g."""
+    n = C.c_int(0)
+    check(_lib.load().bsp_plan_tuning(handle, C.byref(n), None, None, 0))
+    side = (C.c_int * max(n.value, 1))()
+    mult = (C.c_int * max(n.value, 1))()
+    check(_lib.load().bsp_plan_tuning(handle, C.byref(n), side, mult, n.value))
+    return [(int(side[i]), int(mult[i])) for i in range(n.value)]
+
+
 def bsp_plan_triplets(handle) -> np.ndarray:
     tab = C.POINTER(Triplet)()
     n = C.c_int()
@@ -167,10 +177,11 @@ class Plan:
 
     ng, box_len, edges_kf: grid, box side and shell edges in units of k_f = 2 pi / L;
     n_mu, n_t: (mu, t) cells; rsd/beta: linear RSD along z (Eq. (3.4));
-    precision: 'fp64', 'fp32' or 'mixed_bf16x3'."""
+    precision: 'fp64', 'fp32' or 'mixed_bf16x3'; autotune: time the contraction's voxel split
+    per level at creation and keep the fastest (tensor-core plans)."""
 
     def __init__(self, ng, box_len, edges_kf, n_mu=10, n_t=10, rsd=False, beta=0.0,
-                 precision="fp32", stream=None):
+                 precision="fp32", stream=None, autotune=False):
         self._edges = np.ascontiguousarray(np.asarray(edges_kf, dtype=np.float64))
         desc = PlanDesc()
         desc.ng = int(ng)
@@ -183,6 +194,7 @@ class Plan:
         desc.beta = float(beta)
         desc.precision = PRECISIONS[precision]
         desc.mem_budget_bytes = 0
+        desc.autotune = 1 if autotune else 0
         self.handle = None
         self.handle = bsp_plan_create(desc, stream)
         self.ng, self.box_len, self.n_mu, self.n_t = int(ng), float(box_len), int(n_mu), int(n_t)
@@ -192,6 +204,7 @@ class Plan:
         self.n_triplets, self.n_shells, self.field_bytes, self.device_bytes = bsp_plan_info(self.handle)
         self.triplets = bsp_plan_triplets(self.handle)
         self.ng_eval = bsp_plan_grid(self.handle)
+        self.tuning = bsp_plan_tuning(self.handle)
 
     def close(self):
         if self.handle is not None:
@@ -270,5 +283,5 @@ class Plan:
 
 
 __all__ = ["Plan", "BispecError", "bsp_plan_create", "bsp_plan_destroy", "bsp_plan_info",
-           "bsp_plan_triplets", "bsp_plan_grid", "bsp_shell_fields", "bsp_contract", "bsp_estimate",
+           "bsp_plan_triplets", "bsp_plan_grid", "bsp_plan_tuning", "bsp_shell_fields", "bsp_contract", "bsp_estimate",
            "bsp_estimate_host", "bsp_estimate_batched", "Batch", "bsp_spectrum", "bsp_grad", "bsp_last_sums", "bsp_plan_check", "bsp_version", "TRIPLET_DTYPE"]

@@ -99,13 +99,19 @@ struct ContractLevel {
   int* d_tc_map = nullptr;
   int* d_tc_bins = nullptr;
   std::vector<int> tc_off;    // partial-sum entry of each of the level's bins
+  int gridy_cap = 0;          // voxel blocks the partial-sum buffer holds
+  int tune_mult = 1;          // blocks per M tile / SM count chosen by the autotuner (1 without it)
   double* tc_partial = nullptr;
   long long nvox() const { return (long long)g * g * g; }
 };
 
+constexpr int kNumTune = 3;
+constexpr int kTuneMults[kNumTune] = {1, 2, 4};
+
 struct bsp_plan {
   // description
   int ng = 0, ns = 0, n_mu = 0, n_t = 0, rsd = 0, prec = 0;
+  int autotune = 0;
   int ngs = 0;              // side of the evaluation grid (<= ng), see choose_eval_grid
   double sum_scale = 1.0;   // (ng / ngs)^3: sums over the ng^3 grid from sums over ngs^3
   double box_len = 0.0, beta = 0.0;
@@ -445,6 +451,7 @@ bsp_status host_plan(bsp_plan* p, const bsp_plan_desc* d) {
   p->rsd = d->rsd;
   p->beta = d->rsd ? d->beta : 0.0;
   p->prec = d->precision;
+  p->autotune = d->autotune;
   p->box_len = d->box_len;
   p->edges.assign(d->edges_kf, d->edges_kf + d->n_shells + 1);
   p->q.resize(p->ns + 1);
@@ -513,6 +520,61 @@ long long g1_elems(const bsp_plan* p) {
 long long g2_elems(const bsp_plan* p) {
   const ShellGeom& g = p->geom.back();
   return g.g2_off + (long long)p->ngs * p->ngs * g.r;
+}
+
+// Contraction autotuner (plans created with autotune = 1): for every tensor-core level, time its
+// kernel on the plan's own buffers with the voxel range of each M tile split over m x (SM count)
+// blocks, m in kTuneMults (fewer when the level has fewer 128-voxel chunks), 3 launches after one
+// warm-up each, and keep the fastest split. More blocks than SMs trade partial sums and block
+// start-up for a shorter tail. The values computed are the same for every split up to the
+// order of the FP64 cross-block sums.
+bsp_status autotune_levels(bsp_plan* p, cudaStream_t s) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  BSP_CUDA(cudaEventCreate(&e0));
+  cudaError_t ce = cudaEventCreate(&e1);
+  if (ce != cudaSuccess) { cudaEventDestroy(e0); return cuda_fail(ce, "cudaEventCreate"); }
+  bsp_status st = BSP_OK;
+  for (ContractLevel& L : p->levels) {
+    if (L.mtiles == 0) continue;
+    const long long chunks = L.nvox() / kTcVoxelChunk;
+    float best = 1e30f;
+    long long best_vpb = L.vpb;
+    int best_gy = L.gridy, best_m = 1;
+    for (int t = 0; t < kNumTune && st == BSP_OK; ++t) {
+      const long long gy = std::min<long long>((long long)kTuneMults[t] * std::max(1, p->n_sm), chunks);
+      const long long vpb = ((chunks + gy - 1) / gy) * kTcVoxelChunk;
+      const int gridy = (int)((L.nvox() + vpb - 1) / vpb);
+      if (gridy > L.gridy_cap && gridy > L.gridy) continue;
+      TcArgs a{};
+      a.nvox = L.nvox();
+      a.ns = (int)L.shells.size();
+      a.np = L.np;
+      a.pair_ab = L.d_tc_pairs;
+      a.n_mtiles = L.mtiles;
+      a.gridy = gridy;
+      a.vox_per_block = vpb;
+      a.partial = L.tc_partial;
+      a.error = p->d_error;
+      if ((st = launch_contract_tc(a, &L.tmap, s)) != BSP_OK) break;
+      if ((ce = cudaEventRecord(e0, s)) != cudaSuccess) { st = cuda_fail(ce, "cudaEventRecord"); break; }
+      for (int r = 0; r < 3 && st == BSP_OK; ++r) st = launch_contract_tc(a, &L.tmap, s);
+      if (st != BSP_OK) break;
+      if ((ce = cudaEventRecord(e1, s)) != cudaSuccess || (ce = cudaEventSynchronize(e1)) != cudaSuccess) {
+        st = cuda_fail(ce, "autotune timing");
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) { best = ms; best_vpb = vpb; best_gy = gridy; best_m = kTuneMults[t]; }
+    }
+    L.vpb = best_vpb;
+    L.gridy = best_gy;
+    L.tune_mult = best_m;
+    if (st != BSP_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return st;
 }
 
 // Contraction levels (see ContractLevel): each pair (a, b) of the kept bins goes to the smallest
@@ -599,11 +661,14 @@ bsp_status build_levels(bsp_plan* p, cudaStream_t s) {
       long long gy = std::min<long long>(std::max(1, p->n_sm), chunks);
       L.vpb = ((chunks + gy - 1) / gy) * kTcVoxelChunk;
       L.gridy = (int)((L.nvox() + L.vpb - 1) / L.vpb);
+      // partial sums sized for the largest split the autotuner may pick
+      const long long gmax = p->autotune ? std::min<long long>((long long)kTuneMults[kNumTune - 1] * std::max(1, p->n_sm), chunks) : gy;
+      L.gridy_cap = (int)((L.nvox() + ((chunks + gmax - 1) / gmax) * kTcVoxelChunk - 1) / (((chunks + gmax - 1) / gmax) * kTcVoxelChunk));
       if ((st = dev_upload(p, pab, &L.d_tc_pairs, s)) != BSP_OK) return st;
       L.tc_off = tmap;
       if ((st = dev_upload(p, tmap, &L.d_tc_map, s)) != BSP_OK) return st;
       if ((st = dev_upload(p, L.bins, &L.d_tc_bins, s)) != BSP_OK) return st;
-      if ((st = dev_alloc(p, tc_partial_doubles(std::max(L.mtiles, 1), L.gridy, L.np) * sizeof(double), &tmp)) != BSP_OK)
+      if ((st = dev_alloc(p, tc_partial_doubles(std::max(L.mtiles, 1), std::max(L.gridy, L.gridy_cap), L.np) * sizeof(double), &tmp)) != BSP_OK)
         return st;
       L.tc_partial = static_cast<double*>(tmp);
     } else {
@@ -641,6 +706,9 @@ bsp_status build_levels(bsp_plan* p, cudaStream_t s) {
       zt.push_back(L.stride);
     }
     p->levels.push_back(std::move(L));
+  }
+  if (p->prec == BSP_MIXED_BF16X3 && p->autotune) {
+    if ((st = autotune_levels(p, s)) != BSP_OK) return st;
   }
   if (p->prec == BSP_MIXED_BF16X3) {
     std::vector<TcBin> tb(p->trips.size());
@@ -1192,6 +1260,16 @@ bsp_status bsp_plan_info(const bsp_plan* p, int* n_triplets, int* n_shells, size
   if (n_shells) *n_shells = p->ns;
   if (field_bytes) *field_bytes = p->field_bytes();
   if (device_bytes) *device_bytes = p->dev_bytes;
+  return BSP_OK;
+}
+
+bsp_status bsp_plan_tuning(const bsp_plan* p, int* n_levels, int* level_side, int* blocks_mult, int max_levels) {
+  if (!p || !n_levels) return fail(BSP_ERR_INVALID_ARG, "NULL argument");
+  *n_levels = (int)p->levels.size();
+  for (int l = 0; l < (int)p->levels.size() && l < max_levels; ++l) {
+    if (level_side) level_side[l] = p->levels[l].g;
+    if (blocks_mult) blocks_mult[l] = p->prec == BSP_MIXED_BF16X3 ? p->levels[l].tune_mult : 0;
+  }
   return BSP_OK;
 }
 

@@ -67,3 +67,12 @@ def test_ng256_fp32_sampled_bins(lib):
     picks = [-1, -3, -40, 600, 0, 11]
     cond, rel = _sampled(lib, 256, 24, 64.0, 1.5, 0.05, 3, None, "fp32", picks)
     assert np.max(cond) < 1e-4, (cond, rel)
+
+
+def test_ng768_fp32_forward_sampled_bins(lib):
+    """The forward-only Ng=768 FP32 workload (24 shells k_f..192 k_f): every field stays
+    resident (24 x 768^3 FP32 = 43.5 GB); bins of the largest, a middle and the smallest k1
+    shell against the oracle."""
+    picks = [-1, -2, 300, 0]
+    cond, rel = _sampled(lib, 768, 24, 192.0, 1.5, 0.05, 7, None, "fp32", picks)
+    assert np.max(cond) < 1e-4, (cond, rel)

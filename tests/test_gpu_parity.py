@@ -212,3 +212,23 @@ def test_mixed_contract_on_oracle_fields(lib):
     msum = gp.contract(torch.from_numpy(stack).cuda()).cpu().numpy()
     gp.check()
     assert np.max(np.abs(msum - exact) / res["asum"]) < 1e-4
+
+
+def test_autotuned_plan_matches(lib):
+    """The autotuner only changes how each level's voxels are split over blocks: the estimate
+    agrees with the untuned plan to the FP32 partial-sum rounding (condition-scaled)."""
+    ng = 128
+    edges = _edges(ng, 20, 32.0)
+    spec = _spec(ng, 1.5, 0.05, 21, c64=True)
+    pl, res = _oracle(spec, ng, edges, with_abs=True)
+    d = torch.from_numpy(spec).cuda()
+    a = lib.Plan(ng, float(ng), edges, precision="mixed_bf16x3")
+    b = lib.Plan(ng, float(ng), edges, precision="mixed_bf16x3", autotune=True)
+    assert [g for g, _ in a.tuning] == [g for g, _ in b.tuning]
+    assert all(m in (1, 2, 4) for _, m in b.tuning)
+    ba = a.estimate(d)[0].cpu().numpy()
+    bb = b.estimate(d)[0].cpu().numpy()
+    a.check()
+    b.check()
+    assert np.max(np.abs(ba - bb) / res["b_scale"]) < 1e-5
+    assert np.max(_cond_err(bb, res)) < 1e-4
