@@ -353,6 +353,7 @@ bsp_status run_passes(const bsp_plan* p, const void* spec, int rsd, void* tw, vo
                       void* fields, const Item* xi, int nxi, const Item* yi, int nyi, const Item* zi,
                       int nzi, int lines_xy, int lines_z, cudaStream_t s) {
   PassArgs a{};
+  a.n_sm = p->n_sm;
   a.spec = spec;
   a.g1 = g1;
   a.g2 = g2;
@@ -884,6 +885,7 @@ int contract_launches(const bsp_plan* p) {
 template <typename T>
 bsp_status plan_passes(bsp_plan* p, const void* spec, void* fields, cudaStream_t s, cudaEvent_t* ev, bool split = false) {
   PassArgs a{};
+  a.n_sm = p->n_sm;
   a.spec = spec;
   a.g1 = p->g1;
   a.g2 = p->g2;
@@ -1469,6 +1471,7 @@ bsp_status bsp_spectrum(bsp_plan* p, const float* delta_x, void* spec_out, void*
   bsp_status st = ball_setup(p, s);
   if (st != BSP_OK) return st;
   PassArgs b{};
+  b.n_sm = p->n_sm;
   b.g1 = p->g1b;
   b.g2 = p->g2b;
   b.fields = spec_out;
@@ -1509,6 +1512,7 @@ bsp_status bsp_grad(bsp_plan* p, const void* spec, const double* dl_db, float* d
   if (st != BSP_OK) return st;
   // forward transforms of G_n, kept on each shell's modes: conj(.) K (ng/S)^3 into the ng spectrum
   PassArgs a{};
+  a.n_sm = p->n_sm;
   a.g1 = p->g1;
   a.g2 = p->g2;
   a.fields = p->d_grad_spec;
@@ -1531,6 +1535,7 @@ bsp_status bsp_grad(bsp_plan* p, const void* spec, const double* dl_db, float* d
   if (st != BSP_OK) return st;
   // one pruned inverse transform of the whole ball on the ng grid
   PassArgs b{};
+  b.n_sm = p->n_sm;
   b.spec = p->d_grad_spec;
   b.g1 = p->g1b;
   b.g2 = p->g2b;

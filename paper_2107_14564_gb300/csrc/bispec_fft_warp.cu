@@ -162,8 +162,13 @@ template <int N> struct XY {
   static constexpr int kThreads = kLines * kLpl;
 };
 
+// Block b takes items b, b + gridDim.x, ... The Y pass runs persistent blocks: the input tile of
+// the next item is fetched with cp.async (zero-filled outside the shell) into the second of two
+// tile buffers while the current item is transformed, so its global-load latency is hidden. The
+// X pass, whose tiles lie mostly outside the shell (few loads), runs one item per block with
+// plain loads (more resident blocks, one tile buffer).
 template <int N, bool XPASS>
-__global__ void __launch_bounds__(XY<N>::kThreads) xy_warp_kernel(PassArgs a) {
+__global__ void __launch_bounds__(XY<N>::kThreads, XPASS ? 4 : 3) xy_warp_kernel(PassArgs a, int n_items) {
   constexpr int LPL = XY<N>::kLpl;
   constexpr int NT = XY<N>::kThreads;
   constexpr int E = N / LPL;
@@ -171,93 +176,116 @@ __global__ void __launch_bounds__(XY<N>::kThreads) xy_warp_kernel(PassArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* tw = reinterpret_cast<float2*>(smem_raw);  // N entries exp(2 pi i t / N)
   float2* bufs = tw + N;                               // kLines x kBufLd
-  float2* tile = bufs + (size_t)kLines * kBufLd;       // (2r-1) x kTileLd
-  const Item it = a.items[blockIdx.x];
-  const ShellGeom g = a.geom[it.n];
-  const int r = g.r;
-  const int w = 2 * r - 1;
+  float2* tiles = bufs + (size_t)kLines * kBufLd;      // 2 x (2 rmax) x kTileLd
+  const int tile_elems = 2 * a.rmax * kTileLd;
   const int tid = threadIdx.x;
   for (int i = tid; i < N; i += NT) tw[i] = static_cast<const float2*>(a.stw)[i];
-  // ---- input tile [row = k + r - 1][line]
-  if (XPASS) {
-    const float2* spec = static_cast<const float2*>(a.spec);
-    const int ng = a.ng;  // side of the input spectrum's grid
-    const int ky = it.u;
-    const int iy = ky < 0 ? ky + ng : ky;
-    const int hz = ng / 2 + 1;
-    for (int idx = tid; idx < w * kLines; idx += NT) {
-      const int l = idx & (kLines - 1);
-      const int row = idx >> 3;
-      const int mx = row - (r - 1);
-      const int kz = it.v0 + l;
-      const int q = mx * mx + ky * ky + kz * kz;
-      float2 val = make_float2(0.f, 0.f);
-      if (l < it.cnt && q >= g.qlo && q < g.qhi) {
-        const int ix = mx < 0 ? mx + ng : mx;
-        val = spec ? spec[((long long)ix * ng + iy) * hz + kz] : make_float2(1.f, 0.f);
-        if (a.rsd) {
-          const float fac = (float)(1.0 + a.beta * (double)(kz * kz) / (double)q);
-          val.x *= fac;
-          val.y *= fac;
+  // ---- input tile [row = k + r - 1][line] of an item: issue the copies (one commit group)
+  auto issue = [&](int item, float2* tile) {
+    const Item it = a.items[item];
+    const ShellGeom g = a.geom[it.n];
+    const int r = g.r;
+    const int w = 2 * r - 1;
+    if (XPASS) {
+      const float2* spec = static_cast<const float2*>(a.spec);
+      const int ng = a.ng;  // side of the input spectrum's grid
+      const int ky = it.u;
+      const int iy = ky < 0 ? ky + ng : ky;
+      const int hz = ng / 2 + 1;
+      for (int idx = tid; idx < w * kLines; idx += NT) {
+        const int l = idx & (kLines - 1);
+        const int row = idx >> 3;
+        const int mx = row - (r - 1);
+        const int kz = it.v0 + l;
+        const int q = mx * mx + ky * ky + kz * kz;
+        // one item per block (nothing to overlap): plain loads, shell mask and Kaiser factor
+        float2 val = make_float2(0.f, 0.f);
+        if (l < it.cnt && q >= g.qlo && q < g.qhi) {
+          const int ix = mx < 0 ? mx + ng : mx;
+          val = spec ? spec[((long long)ix * ng + iy) * hz + kz] : make_float2(1.f, 0.f);
+          if (a.rsd) {
+            const float fac = (float)(1.0 + a.beta * (double)(kz * kz) / (double)q);
+            val.x *= fac;
+            val.y *= fac;
+          }
         }
+        tile[row * kTileLd + l] = val;
       }
-      tile[row * kTileLd + l] = val;
+    } else {
+      const float2* g1 = static_cast<const float2*>(a.g1) + g.g1_off;
+      const int x = it.u;
+      for (int idx = tid; idx < w * kLines; idx += NT) {
+        const int l = idx & (kLines - 1);
+        const int row = idx >> 3;
+        const int ky = row - (r - 1);
+        const int kz = it.v0 + l;
+        const bool in = l < it.cnt && ky * ky + kz * kz < g.qhi;
+        const float2* src = in ? g1 + ((long long)x * w + row) * r + kz : g1;
+        ptx::cp_async8_zfill(tile + row * kTileLd + l, src, in ? 8u : 0u);
+      }
     }
-  } else {
-    const float2* g1 = static_cast<const float2*>(a.g1) + g.g1_off;
-    const int x = it.u;
-    for (int idx = tid; idx < w * kLines; idx += NT) {
+    ptx::cp_async_commit();
+  };
+  int k = 0;
+  if (blockIdx.x < n_items) issue(blockIdx.x, tiles);
+  // the X pass: exactly one item per block (gridDim.x == n_items), no loop
+  const int stride = XPASS ? n_items : (int)gridDim.x;
+  for (int item = blockIdx.x; item < n_items; item += stride, ++k) {
+    float2* tile = tiles + (size_t)(k & 1) * tile_elems;
+    const int next = item + stride;
+    if (!XPASS && next < n_items) {
+      issue(next, tiles + (size_t)((k + 1) & 1) * tile_elems);
+      ptx::cp_async_wait<1>();  // this item's copies (issued one iteration earlier) have landed
+    } else {
+      ptx::cp_async_wait<0>();
+    }
+    const Item it = a.items[item];
+    const ShellGeom g = a.geom[it.n];
+    const int r = g.r;
+    const int w = 2 * r - 1;
+    __syncthreads();  // the tile is complete; the previous item's read-out of bufs is done
+    // ---- one line per LPL lanes
+    {
+      constexpr int R1 = first_radix<N>();
+      constexpr int BPL = N / (R1 * LPL);
+      const int l = tid / LPL;
+      const int lane = tid & (LPL - 1);
+      float2 v[E];
+#pragma unroll
+      for (int b = 0; b < BPL; ++b)
+#pragma unroll
+        for (int rr = 0; rr < R1; ++rr) {
+          const int pos = lane + b * LPL + rr * (N / R1);
+          const int kk = pos < N / 2 ? pos : pos - N;
+          const int row = kk + r - 1;
+          v[b * R1 + rr] = (row >= 0 && row < w) ? tile[row * kTileLd + l] : make_float2(0.f, 0.f);
+        }
+      float2* buf = bufs + (size_t)l * kBufLd;
+      warp_fft_from<N, LPL, 0, 1>(v, buf, lane, tw);
+      constexpr int RL = last_radix<N>();
+      constexpr int BPLL = N / (RL * LPL);
+      __syncwarp();
+#pragma unroll
+      for (int b = 0; b < BPLL; ++b)
+#pragma unroll
+        for (int rr = 0; rr < RL; ++rr) buf[padn<N>(lane + b * LPL + rr * (N / RL))] = v[b * RL + rr];
+    }
+    __syncthreads();
+    // ---- output tile -> global, contiguous along k_z
+    float2* out;
+    long long row_stride;
+    if (XPASS) {
+      out = static_cast<float2*>(a.g1) + g.g1_off + (long long)(it.u + r - 1) * r + it.v0;
+      row_stride = (long long)w * r;
+    } else {
+      out = static_cast<float2*>(a.g2) + g.g2_off + (long long)it.u * N * r + it.v0;
+      row_stride = r;
+    }
+    for (int idx = tid; idx < N * kLines; idx += NT) {
       const int l = idx & (kLines - 1);
-      const int row = idx >> 3;
-      const int ky = row - (r - 1);
-      const int kz = it.v0 + l;
-      float2 val = make_float2(0.f, 0.f);
-      if (l < it.cnt && ky * ky + kz * kz < g.qhi) val = g1[((long long)x * w + row) * r + kz];
-      tile[row * kTileLd + l] = val;
+      const int y = idx >> 3;
+      if (l < it.cnt) out[y * row_stride + l] = bufs[(size_t)l * kBufLd + padn<N>(y)];
     }
-  }
-  __syncthreads();
-  // ---- one line per LPL lanes
-  {
-    constexpr int R1 = first_radix<N>();
-    constexpr int BPL = N / (R1 * LPL);
-    const int l = tid / LPL;
-    const int lane = tid & (LPL - 1);
-    float2 v[E];
-#pragma unroll
-    for (int b = 0; b < BPL; ++b)
-#pragma unroll
-      for (int rr = 0; rr < R1; ++rr) {
-        const int pos = lane + b * LPL + rr * (N / R1);
-        const int k = pos < N / 2 ? pos : pos - N;
-        const int row = k + r - 1;
-        v[b * R1 + rr] = (row >= 0 && row < w) ? tile[row * kTileLd + l] : make_float2(0.f, 0.f);
-      }
-    float2* buf = bufs + (size_t)l * kBufLd;
-    warp_fft_from<N, LPL, 0, 1>(v, buf, lane, tw);
-    constexpr int RL = last_radix<N>();
-    constexpr int BPLL = N / (RL * LPL);
-    __syncwarp();
-#pragma unroll
-    for (int b = 0; b < BPLL; ++b)
-#pragma unroll
-      for (int rr = 0; rr < RL; ++rr) buf[padn<N>(lane + b * LPL + rr * (N / RL))] = v[b * RL + rr];
-  }
-  __syncthreads();
-  // ---- output tile -> global, contiguous along k_z
-  float2* out;
-  long long row_stride;
-  if (XPASS) {
-    out = static_cast<float2*>(a.g1) + g.g1_off + (long long)(it.u + r - 1) * r + it.v0;
-    row_stride = (long long)w * r;
-  } else {
-    out = static_cast<float2*>(a.g2) + g.g2_off + (long long)it.u * N * r + it.v0;
-    row_stride = r;
-  }
-  for (int idx = tid; idx < N * kLines; idx += NT) {
-    const int l = idx & (kLines - 1);
-    const int y = idx >> 3;
-    if (l < it.cnt) out[y * row_stride + l] = bufs[(size_t)l * kBufLd + padn<N>(y)];
   }
 }
 
@@ -542,13 +570,20 @@ bsp_status launch_zf(const PassArgs& a, const float* gfield, long long n_lines, 
 }
 
 template <int N, bool XPASS>
-bsp_status launch_xy(const PassArgs& a, int n_items, cudaStream_t s) {
+bsp_status launch_xy(const PassArgs& a, int n_items, int n_sm, cudaStream_t s) {
   if (n_items == 0) return BSP_OK;
-  // the tile holds 2 r - 1 rows of the largest shell
+  // tiles of 2 r - 1 rows of the largest shell: two for persistent blocks, one otherwise
+  const int ntiles = XPASS ? 1 : 2;
   const size_t smem =
-      ((size_t)N + (size_t)kLines * line_ld<N>() + (size_t)(2 * a.rmax) * kTileLd) * sizeof(float2);
+      ((size_t)N + (size_t)kLines * line_ld<N>() + (size_t)ntiles * (2 * a.rmax) * kTileLd) * sizeof(float2);
   BSP_CUDA(cudaFuncSetAttribute(xy_warp_kernel<N, XPASS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  xy_warp_kernel<N, XPASS><<<n_items, XY<N>::kThreads, smem, s>>>(a);
+  long long blocks = n_items;
+  if (!XPASS) {
+    int per_sm = 0;
+    BSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, xy_warp_kernel<N, XPASS>, XY<N>::kThreads, smem));
+    blocks = std::min<long long>((long long)std::max(per_sm, 1) * std::max(n_sm, 1), n_items);
+  }
+  xy_warp_kernel<N, XPASS><<<(unsigned)blocks, XY<N>::kThreads, smem, s>>>(a, n_items);
   BSP_CUDA(cudaGetLastError());
   return BSP_OK;
 }
@@ -608,7 +643,7 @@ int warp_fft_lines() { return kLines; }
 
 bsp_status launch_warp_xpass(const PassArgs& a, int n_items, cudaStream_t s) {
   switch (a.ngs) {
-#define X(S) case S: return launch_xy<S, true>(a, n_items, s);
+#define X(S) case S: return launch_xy<S, true>(a, n_items, a.n_sm, s);
     BSP_WARP_SIZES(X)
 #undef X
   }
@@ -617,7 +652,7 @@ bsp_status launch_warp_xpass(const PassArgs& a, int n_items, cudaStream_t s) {
 
 bsp_status launch_warp_ypass(const PassArgs& a, int n_items, cudaStream_t s) {
   switch (a.ngs) {
-#define X(S) case S: return launch_xy<S, false>(a, n_items, s);
+#define X(S) case S: return launch_xy<S, false>(a, n_items, a.n_sm, s);
     BSP_WARP_SIZES(X)
 #undef X
   }

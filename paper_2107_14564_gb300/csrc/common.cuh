@@ -75,6 +75,7 @@ struct PassArgs {
   double beta;
   FftStages st;           // stage list of this pass's line length
   int rmax;               // largest r of all shells
+  int n_sm;               // SMs of the device (grid size of the persistent warp kernels)
   long long split_lo;     // warp Z pass: 0 writes FP32 fields; otherwise bf16 high parts [n][x][y][z]
                           // at `fields` and low parts split_lo 32-bit words further (split fields)
   // split warp Z pass: also write the split fields of the coarser contraction levels
