@@ -309,7 +309,7 @@ def run_ours(args, w):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
     e2e = {"value": bins / e2e_s, "unit": "bins/s",
-           "h2d_bytes_per_step": int(spec_np.nbytes),
+           "h2d_bytes_per_step": int(plan.host_input_bytes),  # the spectrum box the shells reach
            "d2h_bytes_per_step": int(8 * (plan.n_triplets + plan.n_shells * w["n_mu"] * w["n_t"]))}
 
     plain = None

@@ -151,8 +151,11 @@ BSP_API bsp_status bsp_estimate(bsp_plan* plan, const void* spec, double* b_trip
                         void* stream);
 
 /* bsp_estimate from HOST buffers: copies the half spectrum host->device on `stream`, runs the
- * estimator and copies b_triplet (and b_grid if not NULL) back to the host. Pinned host memory
- * gives asynchronous copies; the call synchronises `stream` before it returns. */
+ * estimator and copies b_triplet (and b_grid if not NULL) back to the host. Only the modes the
+ * shells can reach are copied and read: the box |m_x|, |m_y| <= r - 1, 0 <= m_z <= r - 1 of the
+ * outermost shell (Sec. 2.1; bsp_plan_host_input_bytes gives its size), so spec_host's other
+ * entries may hold anything. Pinned host memory gives asynchronous copies; the call
+ * synchronises `stream` before it returns. */
 BSP_API bsp_status bsp_estimate_host(bsp_plan* plan, const void* spec_host, double* b_triplet_host,
                              double* b_grid_host, void* stream);
 
@@ -235,6 +238,9 @@ BSP_API bsp_status bsp_timing_read(bsp_plan* plan, double* ms, int* n_calls, lon
  * columns x voxels for the split-BF16 tensor-core GEMM, summed over the contraction levels.
  * Host-side, no GPU work. */
 BSP_API bsp_status bsp_plan_stage_work(const bsp_plan* plan, double* bytes, double* flops);
+
+/* Bytes bsp_estimate_host copies host->device per call (the spectrum box of the outermost shell). */
+BSP_API bsp_status bsp_plan_host_input_bytes(const bsp_plan* plan, size_t* bytes);
 
 /* Limits of bsp_triple_sums_noalloc (its scratch array has a fixed size). */
 #define BSP_NOALLOC_MAX_TRIPLETS 4096

@@ -52,6 +52,12 @@ def bsp_plan_grid(handle) -> int:
     return n.value
 
 
+def bsp_plan_host_input_bytes(handle) -> int:
+    n = C.c_size_t(0)
+    check(_lib.load().bsp_plan_host_input_bytes(handle, C.byref(n)))
+    return int(n.value)
+
+
 def bsp_plan_tuning(handle):
     """[(level side g, blocks per M tile / SM count)] in ascending g."""
     n = C.c_int(0)
@@ -205,6 +211,7 @@ class Plan:
         self.triplets = bsp_plan_triplets(self.handle)
         self.ng_eval = bsp_plan_grid(self.handle)
         self.tuning = bsp_plan_tuning(self.handle)
+        self.host_input_bytes = bsp_plan_host_input_bytes(self.handle)
 
     def close(self):
         if self.handle is not None:
@@ -283,5 +290,5 @@ class Plan:
 
 
 __all__ = ["Plan", "BispecError", "bsp_plan_create", "bsp_plan_destroy", "bsp_plan_info",
-           "bsp_plan_triplets", "bsp_plan_grid", "bsp_plan_tuning", "bsp_shell_fields", "bsp_contract", "bsp_estimate",
+           "bsp_plan_triplets", "bsp_plan_grid", "bsp_plan_tuning", "bsp_plan_host_input_bytes", "bsp_shell_fields", "bsp_contract", "bsp_estimate",
            "bsp_estimate_host", "bsp_estimate_batched", "Batch", "bsp_spectrum", "bsp_grad", "bsp_last_sums", "bsp_plan_check", "bsp_version", "TRIPLET_DTYPE"]

@@ -1409,7 +1409,26 @@ bsp_status bsp_estimate_host(bsp_plan* p, const void* spec_host, double* b_tripl
     if (st != BSP_OK) return st;
     p->bgrid_dev = static_cast<double*>(t);
   }
-  BSP_CUDA(cudaMemcpyAsync(p->spec_dev, spec_host, p->spec_bytes(), cudaMemcpyHostToDevice, s));
+  // Only the modes the shells can reach are read by the estimator: |m_x|, |m_y| <= R - 1 and
+  // 0 <= m_z <= R - 1 with R = r of the outermost shell. Copy that box (four boxes in the
+  // wrapped index ranges); the rest of the device copy is never read.
+  {
+    const int ng = p->ng, hz = ng / 2 + 1, R = p->rmax;
+    const size_t ce = 2 * p->elem();
+    const int lo[2] = {0, ng - (R - 1)}, len[2] = {R, R - 1};
+    for (int bx = 0; bx < 2; ++bx)
+      for (int by = 0; by < 2; ++by) {
+        if (len[bx] <= 0 || len[by] <= 0) continue;
+        cudaMemcpy3DParms m{};
+        m.srcPtr = make_cudaPitchedPtr(const_cast<void*>(spec_host), (size_t)hz * ce, (size_t)hz * ce, (size_t)ng);
+        m.dstPtr = make_cudaPitchedPtr(p->spec_dev, (size_t)hz * ce, (size_t)hz * ce, (size_t)ng);
+        m.srcPos = make_cudaPos(0, (size_t)lo[by], (size_t)lo[bx]);
+        m.dstPos = m.srcPos;
+        m.extent = make_cudaExtent((size_t)R * ce, (size_t)len[by], (size_t)len[bx]);
+        m.kind = cudaMemcpyHostToDevice;
+        BSP_CUDA(cudaMemcpy3DAsync(&m, s));
+      }
+  }
   st = bsp_estimate(p, p->spec_dev, p->btrip_dev, b_grid_host ? p->bgrid_dev : nullptr, stream);
   if (st != BSP_OK) return st;
   BSP_CUDA(cudaMemcpyAsync(b_triplet_host, p->btrip_dev, p->trips.size() * sizeof(double),
@@ -1418,6 +1437,13 @@ bsp_status bsp_estimate_host(bsp_plan* p, const void* spec_host, double* b_tripl
     BSP_CUDA(cudaMemcpyAsync(b_grid_host, p->bgrid_dev, (size_t)p->n_cells() * sizeof(double),
                              cudaMemcpyDeviceToHost, s));
   BSP_CUDA(cudaStreamSynchronize(s));
+  return BSP_OK;
+}
+
+bsp_status bsp_plan_host_input_bytes(const bsp_plan* p, size_t* bytes) {
+  if (!p || !bytes) return fail(BSP_ERR_INVALID_ARG, "NULL argument");
+  const size_t R = (size_t)p->rmax;
+  *bytes = (2 * R - 1) * (2 * R - 1) * R * 2 * p->elem();
   return BSP_OK;
 }
 

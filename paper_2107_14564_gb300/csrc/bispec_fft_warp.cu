@@ -374,6 +374,27 @@ __global__ void __launch_bounds__(kZThreads, 4) z_warp_kernel(PassArgs a, long l
           const int j = L.loc[n];
           if (j < 0) continue;
           uint16_t* lh = L.dst + (((long long)j * L.g + __float2int_rn(x * L.rt)) * L.g + __float2int_rn(y * L.rt)) * L.g;
+          // power-of-two strides t with t / 2 dividing every element offset b LPL + rr M / RL: a lane
+          // keeps all its even z (z = 2k, k = lane + offset) or none, at z / t = k / (t / 2)
+          constexpr int kG = (LPL % (M / RL) == 0) ? (M / RL) : ((M / RL) % LPL == 0 ? LPL : 1);
+          const int ht = L.t >> 1;
+          if ((L.t & (L.t - 1)) == 0 && kG % ht == 0) {
+            if (lane % ht == 0) {
+              const int sh = __ffs(ht) - 1;
+#pragma unroll
+              for (int b = 0; b < BPLL; ++b)
+#pragma unroll
+                for (int rr = 0; rr < RL; ++rr) {
+                  const int zz = (lane + b * LPL + rr * (M / RL)) >> sh;
+                  const float2 x2 = v[b * RL + rr];
+                  uint32_t h, lo;
+                  ptx::split_bf16x2(ptx::f2_pack(x2.x, x2.y), h, lo);
+                  lh[zz] = (uint16_t)(h & 0xFFFFu);
+                  lh[L.lo_off + zz] = (uint16_t)(lo & 0xFFFFu);
+                }
+            }
+            continue;
+          }
 #pragma unroll
           for (int b = 0; b < BPLL; ++b)
 #pragma unroll

@@ -232,3 +232,23 @@ def test_autotuned_plan_matches(lib):
     b.check()
     assert np.max(np.abs(ba - bb) / res["b_scale"]) < 1e-5
     assert np.max(_cond_err(bb, res)) < 1e-4
+
+
+def test_host_entry_reads_only_the_shell_box(lib):
+    """bsp_estimate_host copies only |m_x|, |m_y|, m_z < r of the outermost shell: NaN written
+    everywhere else in the host spectrum changes nothing."""
+    ng = 64
+    edges = _edges(ng, 10)
+    spec = _spec(ng, 1.5, 0.05, 23, c64=True)
+    gp = lib.Plan(ng, float(ng), edges, precision="mixed_bf16x3")
+    b_dev, g_dev = gp.estimate(torch.from_numpy(spec).cuda())
+    pl = P.make_plan(ng, float(ng), edges)
+    r = int(np.sqrt(pl.thresholds[-1] - 1)) + 1
+    m = np.fft.fftfreq(ng, 1.0 / ng).astype(int)
+    inside = (np.abs(m)[:, None, None] < r) & (np.abs(m)[None, :, None] < r) & (np.arange(ng // 2 + 1)[None, None, :] < r)
+    dirty = spec.copy()
+    dirty[~inside] = np.nan
+    assert gp.host_input_bytes == int(inside.sum()) * 8
+    b_h, g_h = gp.estimate_host(torch.from_numpy(dirty).pin_memory())
+    assert np.array_equal(b_h, b_dev.cpu().numpy())
+    assert np.array_equal(np.nan_to_num(g_h, nan=-1.0), np.nan_to_num(g_dev.cpu().numpy(), nan=-1.0))
