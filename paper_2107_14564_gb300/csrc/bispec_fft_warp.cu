@@ -30,14 +30,14 @@ constexpr int kTileLd = kLines + 1; // padded tile row (complex)
 
 // Placement of point i in the per-line exchange buffers, chosen per length and radix list by
 // counting the shared-memory wavefronts of every stage's load and store pattern (64-bit accesses,
-// two half-warp phases): length 384 permutes i by i XOR ((i >> 4) & 3) (no extra space), 96 is
+// two half-warp phases): length 384 permutes i by i XOR ((i >> 3) & 15) (no extra space), 96 is
 // unpadded, the others get one spare slot every 2^shift points (shift 2 for 64, else 4).
 template <int N> struct Pad {
   static constexpr bool kXor = N == 384;
   static constexpr int shift = (kXor || N == 96) ? 0 : (N == 64 ? 2 : 4);
 };
 template <int N> __device__ __forceinline__ int padn(int i) {
-  if constexpr (Pad<N>::kXor) return i ^ ((i >> 4) & 3);
+  if constexpr (Pad<N>::kXor) return i ^ ((i >> 3) & 15);
   return Pad<N>::shift ? i + (i >> Pad<N>::shift) : i;
 }
 template <int N> __host__ __device__ constexpr int pad_len() { return Pad<N>::shift ? N + (N >> Pad<N>::shift) : N; }
@@ -54,7 +54,7 @@ template <> struct Radices<96> { static constexpr int lpl = 8, n = 3; static con
 template <> struct Radices<128> { static constexpr int lpl = 32, n = 4; static constexpr int r[4] = {4, 4, 4, 2}; };
 template <> struct Radices<192> { static constexpr int lpl = 16, n = 3; static constexpr int r[3] = {4, 12, 4}; };
 template <> struct Radices<256> { static constexpr int lpl = 32, n = 3; static constexpr int r[3] = {8, 8, 4}; };
-template <> struct Radices<384> { static constexpr int lpl = 32, n = 4; static constexpr int r[4] = {12, 4, 4, 2}; };
+template <> struct Radices<384> { static constexpr int lpl = 16, n = 3; static constexpr int r[3] = {8, 8, 6}; };
 template <> struct Radices<512> { static constexpr int lpl = 32, n = 3; static constexpr int r[3] = {8, 8, 8}; };
 template <> struct Radices<768> { static constexpr int lpl = 32, n = 3; static constexpr int r[3] = {8, 8, 12}; };
 template <> struct Radices<1024> { static constexpr int lpl = 32, n = 4; static constexpr int r[4] = {8, 8, 8, 2}; };

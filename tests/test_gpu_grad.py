@@ -97,3 +97,23 @@ def test_adjoint_config5_sampled_voxels(lib):
     scale = np.abs(want).max()
     assert np.abs(got.ravel()[vox] - want.ravel()[vox]).max() / scale < 1e-4
     assert np.abs(got - want).max() / scale < 1e-4
+
+
+@pytest.mark.slow
+def test_adjoint_on_a_384_evaluation_grid(lib):
+    """The adjoint's forward transforms at length 384 (16 lanes per line, radices 8, 8, 6): Ng = 384
+    with shells up to 96 k_f puts the evaluation grid at 384. The upstream gradient is non-zero
+    on 12 bins only, so the oracle's adjoint needs only those."""
+    ng = 384
+    _, delta, gp, pl = _setup(lib, ng, 16, 96.0, 8)
+    assert gp.ng_eval == 384
+    trips = [tuple(int(v) for v in t) for t in zip(gp.triplets["a"], gp.triplets["b"], gp.triplets["c"])]
+    g = np.zeros(len(trips))
+    pick = np.linspace(0, len(trips) - 1, 12).astype(int)
+    g[pick] = fieldgen.random_weights(len(pick), 10)
+    want = G.vjp(delta.astype(np.float64), pl, [trips[i] for i in pick], gp.triplets["tsum"][pick], g[pick])
+    spec = gp.spectrum(torch.from_numpy(delta).cuda())
+    got = gp.grad(spec, torch.from_numpy(g).cuda()).cpu().numpy()
+    gp.check()
+    err = np.abs(got - want).max() / np.abs(want).max()
+    assert err < 1e-4, err
