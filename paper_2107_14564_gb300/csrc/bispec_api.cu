@@ -96,8 +96,6 @@ struct ContractLevel {
   int np = 0, mtiles = 0, gridy = 0;
   long long vpb = 0;
   int2* d_tc_pairs = nullptr;
-  int* d_tc_map = nullptr;
-  int* d_tc_bins = nullptr;
   std::vector<int> tc_off;    // partial-sum entry of each of the level's bins
   int gridy_cap = 0;          // voxel blocks the partial-sum buffer holds
   int tune_mult = 1;          // blocks per M tile / SM count chosen by the autotuner (1 without it)
@@ -138,13 +136,6 @@ struct bsp_plan {
   ZLevel* d_zlev = nullptr;
   uint32_t* d_zmask = nullptr;
   int n_zlev = 0;
-  // contraction tables (kept bins)
-  Tile* d_tiles = nullptr;
-  int2* d_pairs = nullptr;
-  int* d_map = nullptr;
-  int ntiles = 0;
-  int gridx = 0;
-  double* partial = nullptr;
   double* msum = nullptr;
   double* tsum = nullptr;
   int* cell_ptr = nullptr;
@@ -157,12 +148,6 @@ struct bsp_plan {
   int nwxi = 0, nwyi = 0;
   int rmax = 0;
   std::vector<ContractLevel> levels;
-  // tensor-core contraction (BSP_MIXED_BF16X3)
-  int tc_np = 0, tc_mtiles = 0, tc_gridy = 0;
-  long long tc_vpb = 0;
-  int2* d_tc_pairs = nullptr;
-  int* d_tc_map = nullptr;
-  double* tc_partial = nullptr;
   int* d_error = nullptr;
   // gradient resources (built by the first bsp_grad call)
   bool grad_ready = false;
@@ -667,8 +652,6 @@ bsp_status build_levels(bsp_plan* p, cudaStream_t s) {
       L.gridy_cap = (int)((L.nvox() + ((chunks + gmax - 1) / gmax) * kTcVoxelChunk - 1) / (((chunks + gmax - 1) / gmax) * kTcVoxelChunk));
       if ((st = dev_upload(p, pab, &L.d_tc_pairs, s)) != BSP_OK) return st;
       L.tc_off = tmap;
-      if ((st = dev_upload(p, tmap, &L.d_tc_map, s)) != BSP_OK) return st;
-      if ((st = dev_upload(p, L.bins, &L.d_tc_bins, s)) != BSP_OK) return st;
       if ((st = dev_alloc(p, tc_partial_doubles(std::max(L.mtiles, 1), std::max(L.gridy, L.gridy_cap), L.np) * sizeof(double), &tmp)) != BSP_OK)
         return st;
       L.tc_partial = static_cast<double*>(tmp);

@@ -328,17 +328,6 @@ __global__ void split_fields_kernel(const float2* __restrict__ src, uint32_t* __
   }
 }
 
-// msum[t] = scale * sum over voxel blocks of partial[y][map[t]], blocks in order.
-__global__ void reduce_tc_kernel(const double* partial, int gridy, long long stride, const int* map, const int* bins,
-                                 int n_out, double* msum, double scale) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n_out) return;
-  const long long off = map[t];
-  double s = 0.0;
-  for (int y = 0; y < gridy; ++y) s += partial[(long long)y * stride + off];
-  msum[bins ? bins[t] : t] = scale * s;
-}
-
 // msum[t] for the bins of all levels: lane l adds blocks y = l, l + 32, ... in order, then the
 // warp adds its 32 partial sums by a fixed butterfly, so the result does not depend on timing.
 __global__ void reduce_tc_all_kernel(const TcBin* __restrict__ bins, int n, double* __restrict__ msum) {
@@ -420,15 +409,6 @@ bsp_status encode_split_map(CUtensorMap* map, void* base, long long nvox, int ro
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail_c(BSP_ERR_CUDA, "cuTensorMapEncodeTiled failed");
-  return BSP_OK;
-}
-
-bsp_status launch_reduce_tc(const TcArgs& a, const int* map, const int* bins, int n_out, double* msum,
-                            double scale, cudaStream_t s) {
-  if (a.n_mtiles == 0 || n_out == 0) return BSP_OK;
-  const long long stride = (long long)a.n_mtiles * 128 * a.np;
-  reduce_tc_kernel<<<(n_out + 255) / 256, 256, 0, s>>>(a.partial, a.gridy, stride, map, bins, n_out, msum, scale);
-  BSP_CUDA(cudaGetLastError());
   return BSP_OK;
 }
 

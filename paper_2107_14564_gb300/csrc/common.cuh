@@ -195,10 +195,6 @@ bsp_status launch_contract_tc(const TcArgs& a, const CUtensorMap* tmap, cudaStre
 bsp_status encode_split_map(CUtensorMap* map, void* base, long long nvox, int rows, int np);
 // Split FP32 fields [ns][nvox] into bf16 planes: hi (n words of two values) at dst, lo at dst + n.
 bsp_status launch_split_fields(const float* src, uint32_t* dst, long long n_words, int n_sm, cudaStream_t s);
-// msum[bins[t]] = scale * sum_y partial[y][map[t]], t < n_out, map[t] = (mtile * 128 + row) * np + c
-// (bins may be null: identity)
-bsp_status launch_reduce_tc(const TcArgs& a, const int* map, const int* bins, int n_out, double* msum,
-                            double scale, cudaStream_t s);
 // One kept bin of the tensor-core contraction: msum[t] = scale * sum_y partial[y * stride + off].
 struct TcBin {
   const double* partial;
