@@ -252,3 +252,51 @@ def test_host_entry_reads_only_the_shell_box(lib):
     b_h, g_h = gp.estimate_host(torch.from_numpy(dirty).pin_memory())
     assert np.array_equal(b_h, b_dev.cpu().numpy())
     assert np.array_equal(np.nan_to_num(g_h, nan=-1.0), np.nan_to_num(g_dev.cpu().numpy(), nan=-1.0))
+
+
+@pytest.mark.parametrize("prec", ["fp32", "mixed_bf16x3"])
+def test_log_spaced_shells(lib, prec):
+    """Shells of growing width (log-spaced edges, Sec. 2.1 allows any ring widths): plan tables
+    and values against the oracle."""
+    ng = 64
+    edges = np.geomspace(1.0, 16.0, 11)
+    spec = _spec(ng, 1.5, 0.05, 24, c64=True)
+    pl, res = _oracle(spec, ng, edges, with_abs=True)
+    gp = lib.Plan(ng, float(ng), edges, precision=prec)
+    _check_plan_tables(gp, res, pl)
+    b, _ = gp.estimate(torch.from_numpy(spec).cuda())
+    gp.check()
+    assert np.max(_cond_err(b.cpu().numpy(), res)) < 1e-4
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "mixed_bf16x3"])
+def test_degenerate_inputs(lib, prec):
+    """One shell (bins (0, 0, 0) only) and a zero field (every sum exactly zero)."""
+    ng = 32
+    dtype = np.complex128 if prec == "fp64" else np.complex64
+    one = lib.Plan(ng, float(ng), [2.0, 6.0], precision=prec)
+    tr = one.triplets
+    assert len(tr) == 1 and (tr["a"][0], tr["b"][0], tr["c"][0]) == (0, 0, 0)
+    spec = _spec(ng, 2.0, 0.1, 25, c64=prec != "fp64")
+    pl, res = _oracle(spec, ng, [2.0, 6.0], with_abs=True)
+    b, _ = one.estimate(torch.from_numpy(spec).cuda())
+    assert abs(b.cpu().numpy()[0] - res["b"][0]) <= (1e-10 if prec == "fp64" else 1e-4) * res["b_scale"][0]
+    many = lib.Plan(ng, float(ng), _edges(ng, 8), precision=prec)
+    zero = torch.zeros((ng, ng, ng // 2 + 1), dtype=torch.from_numpy(np.zeros(1, dtype)).dtype, device="cuda")
+    bz, gz = many.estimate(zero)
+    many.check()
+    assert np.all(bz.cpu().numpy() == 0.0)
+    g = gz.cpu().numpy()
+    assert np.all((g == 0.0) | np.isnan(g))
+
+
+def test_shell_count_limits(lib):
+    """The tensor-core contraction takes at most 64 shells (N <= 64 per MMA); FP32 plans more."""
+    ng = 256
+    edges = np.linspace(1.0, 66.0, 66)                  # 65 shells of width 1
+    with pytest.raises(lib.BispecError) as e:
+        lib.Plan(ng, float(ng), edges, precision="mixed_bf16x3")
+    assert e.value.status == 6                          # BSP_ERR_NOT_SUPPORTED
+    gp = lib.Plan(ng, float(ng), np.linspace(1.0, 64.0, 65), precision="mixed_bf16x3")
+    assert gp.n_shells == 64
+    gp.close()
