@@ -310,7 +310,7 @@ def run_ours(args, w):
         e2e_s = float(t.item())
     e2e = {"value": bins / e2e_s, "unit": "bins/s",
            "h2d_bytes_per_step": int(plan.host_input_bytes),  # the spectrum box the shells reach
-           "d2h_bytes_per_step": int(8 * (plan.n_triplets + plan.n_shells * w["n_mu"] * w["n_t"]))}
+           "d2h_bytes_per_step": int(8 * (plan.n_triplets + plan.n_groups * w["n_mu"] * w["n_t"]))}
 
     plain = None
     if args.precision != "fp32" and not args.no_plain and world == 1:

@@ -64,6 +64,13 @@ typedef enum {
                            FP32 accumulation in tensor memory over short voxel runs, FP64 across */
 } bsp_precision;
 
+typedef enum {
+  BSP_LABEL_SHELL_MEAN = 0,    /* k1, k2, k3 of Eq. (2.4): the mean |k| of the modes of each shell */
+  BSP_LABEL_TRIANGLE_MEAN = 1  /* the mean |k_a|, |k_b|, |k_c| over the bin's closed triangles (the
+                                  bin's average triangle, Sec. 2.1), from FP64 sums of Eq. (2.10)
+                                  with one counting field weighted by |k|; plan time only */
+} bsp_label_k;
+
 typedef struct {
   int ng;                  /* grid points per side; even, 16..1024, of the form 2^p or 3*2^p */
   double box_len;          /* L, the side of the periodic cube (any length unit) */
@@ -78,6 +85,9 @@ typedef struct {
                               its voxels split over 1, 2 and 4 x (SM count) blocks per M tile and
                               keep the fastest (BSP_MIXED_BF16X3 plans; the split changes only the
                               order of the FP64 cross-block sums). No counterpart in the paper. */
+  int k1_merge;            /* (mu, t) cells span this many neighbouring k1 shells (Sec. 2.1, last
+                              paragraph: merging adjacent bins); 0 or 1: one shell per cell group */
+  int label_k;             /* a bsp_label_k: the lengths the labels (mu, t) are formed from */
 } bsp_plan_desc;
 
 /* One bin of triangles (Sec. 2.1): shells a >= b >= c and their labels (Eq. (2.4)). */
@@ -87,7 +97,7 @@ typedef struct {
   int inside;          /* 1 iff (mu, t) satisfies Eq. (2.2) */
   double ntri;         /* N_tri of Eq. (2.9)/(2.10), an integer, ordered triples */
   double tsum;         /* sum_x i_a i_b i_c = Ng^3 N_tri (FP64, as computed) */
-  double k1, k2, k3;   /* mean mode length of shells a, b, c, units of k_f (Sec. 2.1) */
+  double k1, k2, k3;   /* lengths of sides a, b, c (units of k_f) per the plan's bsp_label_k */
   double mu, t;        /* Eq. (2.4), unclamped */
 } bsp_triplet;
 
@@ -144,9 +154,10 @@ BSP_API bsp_status bsp_contract(bsp_plan* plan, const void* fields, double* msum
 
 /* The whole estimator on one field, Eqs. (2.7)-(2.11) and the (mu, t) map:
  *   b_triplet[t] = V_c^3 msum[t] / (V tsum[t])                        (device, n_triplets)
- *   b_grid[a][i_mu][i_t] = V_c^3 sum msum / (V sum tsum) over the kept bins of k1 shell a in
- *   that cell (merged bins, Sec. 2.1 last paragraph); NaN where no bin falls (device,
- *   N_s * n_mu * n_t; may be NULL). spec: device half spectrum, read-only. */
+ *   b_grid[g][i_mu][i_t] = V_c^3 sum msum / (V sum tsum) over the kept bins whose k1 shell a has
+ *   a / k1_merge = g in that cell (merged bins, Sec. 2.1 last paragraph); NaN where no bin falls
+ *   (device, ceil(N_s / k1_merge) * n_mu * n_t; may be NULL). spec: device half spectrum,
+ *   read-only. */
 BSP_API bsp_status bsp_estimate(bsp_plan* plan, const void* spec, double* b_triplet, double* b_grid,
                         void* stream);
 

@@ -81,3 +81,37 @@ def direct_estimate(spec_half: np.ndarray, plan: P.Plan, count_only: bool = Fals
         out_n[(a, b, c)] = int(ntri[key])
         out_m[(a, b, c)] = complex(msum_re[key], msum_im[key])
     return out_m, out_n
+
+
+def direct_mean_k(plan: P.Plan):
+    """{(a, b, c): (mean |k_a|, mean |k_b|, mean |k_c|)} over each bin's triangles (k_f units),
+    by the same enumeration of ordered (k_b, k_c) pairs as direct_estimate."""
+    modes, shell, r = ball_modes(plan)
+    length = np.sqrt((modes * modes).sum(1).astype(np.float64))
+    span = 4 * r + 1
+    table = -np.ones((span, span, span), dtype=np.int64)
+    table[modes[:, 0] + 2 * r, modes[:, 1] + 2 * r, modes[:, 2] + 2 * r] = np.arange(len(modes))
+    ns = plan.ns
+    nbin = ns * ns * ns
+    ntri = np.zeros(nbin, dtype=np.int64)
+    ksum = np.zeros((3, nbin))
+    for ib in range(len(modes)):
+        ka = -(modes[ib][None, :] + modes)
+        ida = table[ka[:, 0] + 2 * r, ka[:, 1] + 2 * r, ka[:, 2] + 2 * r]
+        ok = ida >= 0
+        ic = np.nonzero(ok)[0]
+        ia = ida[ok]
+        sa, sb, sc = shell[ia], shell[ib], shell[ic]
+        keep = (sa >= sb) & (sb >= sc)
+        ia, ic, sa, sc = ia[keep], ic[keep], sa[keep], sc[keep]
+        key = (sa * ns + sb) * ns + sc
+        ntri += np.bincount(key, minlength=nbin)
+        ksum[0] += np.bincount(key, weights=length[ia], minlength=nbin)
+        ksum[1] += np.bincount(key, weights=np.full(len(key), length[ib]), minlength=nbin)
+        ksum[2] += np.bincount(key, weights=length[ic], minlength=nbin)
+    out = {}
+    for key in np.nonzero(ntri)[0]:
+        a, rem = divmod(int(key), ns * ns)
+        b, c = divmod(rem, ns)
+        out[(a, b, c)] = tuple(ksum[:, key] / ntri[key])
+    return out

@@ -12,7 +12,8 @@ Steps, in the paper's order (Sec. 2.2):
         B_abc = V_c^3 sum_x d_a d_b d_c / (V N_tri Ng^3),  N_tri = sum_x i_a i_b i_c / Ng^3,
      so B_abc = V_c^3 sum_x d_a d_b d_c / (V sum_x i_a i_b i_c); Ng^3 cancels.
   5. label every bin with (k1, mu, t) (Eq. (2.4)) and, for the (mu, t) grid, merge the bins
-     of one k1 shell that fall in one cell as one bigger bin of Eq. (2.3):
+     of one k1 shell (or of plan.k1_merge neighbouring k1 shells) that fall in one cell as one
+     bigger bin of Eq. (2.3):
         B_cell = V_c^3 sum_{bins} sum_x d d d / (V sum_{bins} sum_x i i i)
      (Sec. 2.1 last paragraph: merging adjacent bins).
 
@@ -73,6 +74,32 @@ def counting_fields(plan: P.Plan, shells=None, workers: int = -1):
     return shell_fields(ones, plan, shells, workers)
 
 
+def length_fields(plan: P.Plan, shells=None, workers: int = -1):
+    """w_n(x) = sum_{k in n} |k| e^{+i k.x}, |k| in units of k_f: the counting field of
+    Eq. (2.11) with every mode weighted by its length."""
+    ng = plan.ng
+    m = np.fft.fftfreq(ng, d=1.0 / ng)
+    mz = np.arange(ng // 2 + 1, dtype=np.float64)
+    q = m[:, None, None] ** 2 + m[None, :, None] ** 2 + mz[None, None, :] ** 2
+    return shell_fields(np.sqrt(q).astype(np.complex128), plan, shells, workers)
+
+
+def triangle_mean_k(plan: P.Plan, triplets, workers: int = -1) -> np.ndarray:
+    """Per bin (a, b, c): the mean of |k_a|, |k_b| and |k_c| over its closed triangles (k_f
+    units), the size and shape of the bin's average triangle (Sec. 2.1):
+        kbar_1 = sum_x w_a i_b i_c / sum_x i_a i_b i_c   (likewise w_b for kbar_2, w_c for kbar_3),
+    the sums of Eq. (2.10) with one counting field replaced by its length-weighted one."""
+    need = sorted({s for t in triplets for s in t})
+    f = dict(counting_fields(plan, need, workers))
+    f.update({("w", n): v for n, v in length_fields(plan, need, workers).items()})
+    tsum = triple_sums(f, triplets)
+    out = np.empty((len(triplets), 3))
+    for j in range(3):
+        wt = [tuple(("w", s) if i == j else s for i, s in enumerate(t)) for t in triplets]
+        out[:, j] = triple_sums(f, wt) / tsum
+    return out
+
+
 def triple_sums(fields: dict, triplets, absolute: bool = False) -> np.ndarray:
     """sum_x f_a f_b f_c for each (a, b, c) (Eq. (2.7) and Eq. (2.10) numerators).
 
@@ -128,7 +155,8 @@ def estimate(spec_half: np.ndarray, plan: P.Plan, beta: float | None = None,
     msum = triple_sums(dfields, trips)
     norm = plan.vcell ** 3 / plan.volume
     b = norm * msum / tsum
-    labels = P.label_table(plan, trips)
+    kvals = triangle_mean_k(plan, trips, workers) if plan.label_k == "triangle" else None
+    labels = P.label_table(plan, trips, kvals)
     grid, gcount = merge_cells(plan, trips, labels, msum, tsum)
     res = dict(triplets=trips, tsum=tsum, ntri=ntri, msum=msum, b=b, labels=labels,
                grid=grid, grid_count=gcount)
@@ -139,15 +167,17 @@ def estimate(spec_half: np.ndarray, plan: P.Plan, beta: float | None = None,
 
 
 def merge_cells(plan: P.Plan, trips, labels, msum, tsum):
-    """Per (k1 shell, mu cell, t cell): V_c^3 sum M / (V sum T), bins added in list order."""
-    ns, nm, nt = plan.ns, plan.n_mu, plan.n_t
+    """Per (k1 group, mu cell, t cell): V_c^3 sum M / (V sum T), bins added in list order; a
+    group holds plan.k1_merge consecutive k1 shells (the last one fewer)."""
+    ns, nm, nt = plan.n_groups, plan.n_mu, plan.n_t
     num = np.zeros((ns, nm, nt))
     den = np.zeros((ns, nm, nt))
     cnt = np.zeros((ns, nm, nt), dtype=np.int64)
     for (a, _, _), lab, m, t in zip(trips, labels, msum, tsum):
-        num[a, lab["i_mu"], lab["i_t"]] += m
-        den[a, lab["i_mu"], lab["i_t"]] += t
-        cnt[a, lab["i_mu"], lab["i_t"]] += 1
+        gi = a // plan.k1_merge
+        num[gi, lab["i_mu"], lab["i_t"]] += m
+        den[gi, lab["i_mu"], lab["i_t"]] += t
+        cnt[gi, lab["i_mu"], lab["i_t"]] += 1
     norm = plan.vcell ** 3 / plan.volume
     with np.errstate(invalid="ignore", divide="ignore"):
         grid = np.where(cnt > 0, norm * num / den, np.nan)

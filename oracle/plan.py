@@ -114,6 +114,12 @@ class Plan:
     n_mu: int = 10
     n_t: int = 10
     extra: dict = field(default_factory=dict)
+    k1_merge: int = 1              # k1 shells per (mu, t) cell group (Sec. 2.1, merging bins)
+    label_k: str = "shell"         # "shell": k of Eq. (2.4) = shell means; "triangle": bin means
+
+    @property
+    def n_groups(self) -> int:
+        return (self.ns + self.k1_merge - 1) // self.k1_merge
 
     @property
     def ns(self) -> int:
@@ -133,7 +139,7 @@ class Plan:
 
 
 def make_plan(ng: int, box_len: float, edges_kf, n_mu: int = 10, n_t: int = 10,
-              allow_aliasing: bool = False) -> Plan:
+              allow_aliasing: bool = False, k1_merge: int = 1, label_k: str = "shell") -> Plan:
     """Shells, their mode counts and means, and the candidate triplets (Sec. 2.1)."""
     edges = np.asarray(edges_kf, dtype=np.float64)
     if edges.ndim != 1 or len(edges) < 2 or np.any(np.diff(edges) <= 0):
@@ -147,7 +153,12 @@ def make_plan(ng: int, box_len: float, edges_kf, n_mu: int = 10, n_t: int = 10,
     if np.any(nm == 0):
         raise ValueError("a shell holds no modes")
     cand = [t for t in all_triplets(len(thr) - 1) if may_close(thr, *t)]
-    return Plan(ng, float(box_len), edges, thr, nm, kb, cand, n_mu, n_t)
+    if k1_merge < 1:
+        raise ValueError("k1_merge must be >= 1")
+    if label_k not in ("shell", "triangle"):
+        raise ValueError("label_k must be 'shell' or 'triangle'")
+    return Plan(ng, float(box_len), edges, thr, nm, kb, cand, n_mu, n_t, k1_merge=k1_merge,
+                label_k=label_k)
 
 
 def linear_edges(ns: int, lo: float, hi: float) -> np.ndarray:
@@ -155,11 +166,16 @@ def linear_edges(ns: int, lo: float, hi: float) -> np.ndarray:
     return np.linspace(lo, hi, ns + 1)
 
 
-def label_table(plan: Plan, triplets):
-    """Per triplet: (k1, k2, k3) in k_f units, mu, t, cell (i_mu, i_t), in-region flag."""
+def label_table(plan: Plan, triplets, kvals=None):
+    """Per triplet: (k1, k2, k3) in k_f units, mu, t, cell (i_mu, i_t), in-region flag. The
+    lengths are the shells' mean |k| (kbar), or kvals[i] (one row of three per triplet) when
+    given, e.g. the means over each bin's triangles."""
     out = []
-    for (a, b, c) in triplets:
-        k1, k2, k3 = plan.kbar[a], plan.kbar[b], plan.kbar[c]
+    for i, (a, b, c) in enumerate(triplets):
+        if kvals is None:
+            k1, k2, k3 = plan.kbar[a], plan.kbar[b], plan.kbar[c]
+        else:
+            k1, k2, k3 = (float(v) for v in kvals[i])
         mu, t = shape_label(k1, k2, k3)
         im, it = shape_cell(mu, t, plan.n_mu, plan.n_t)
         out.append(dict(a=a, b=b, c=c, k1=k1, k2=k2, k3=k3, mu=mu, t=t,

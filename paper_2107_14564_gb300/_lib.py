@@ -22,7 +22,9 @@ class PlanDesc(C.Structure):
     _fields_ = [("ng", C.c_int), ("box_len", C.c_double), ("n_shells", C.c_int),
                 ("edges_kf", C.POINTER(C.c_double)), ("n_mu", C.c_int), ("n_t", C.c_int),
                 ("rsd", C.c_int), ("beta", C.c_double), ("precision", C.c_int),
-                ("mem_budget_bytes", C.c_size_t), ("autotune", C.c_int)]
+                ("mem_budget_bytes", C.c_size_t), ("autotune", C.c_int),
+                ("k1_merge", C.c_int),
+                ("label_k", C.c_int)]
 
 
 class Triplet(C.Structure):

@@ -152,7 +152,7 @@ class Batch:
             p._check_spec(sp)
         dev = self.specs[0].device
         self.b = [torch.empty(p.n_triplets, dtype=torch.float64, device=dev) for p in self.plans]
-        self.grid = [torch.empty((p.n_shells, p.n_mu, p.n_t), dtype=torch.float64, device=dev)
+        self.grid = [torch.empty((p.n_groups, p.n_mu, p.n_t), dtype=torch.float64, device=dev)
                      for p in self.plans] if with_grid else None
         out = C.c_void_p()
         grids = _ptr_array(self.grid) if self.grid is not None else None
@@ -184,10 +184,14 @@ class Plan:
     ng, box_len, edges_kf: grid, box side and shell edges in units of k_f = 2 pi / L;
     n_mu, n_t: (mu, t) cells; rsd/beta: linear RSD along z (Eq. (3.4));
     precision: 'fp64', 'fp32' or 'mixed_bf16x3'; autotune: time the contraction's voxel split
-    per level at creation and keep the fastest (tensor-core plans)."""
+    per level at creation and keep the fastest (tensor-core plans); k1_merge: (mu, t) cells span
+    this many neighbouring k1 shells (b_grid has ceil(Ns / k1_merge) groups); label_k: 'shell'
+    forms (mu, t) from the shells' mean |k|, 'triangle' from the mean sides of each bin's
+    triangles."""
 
     def __init__(self, ng, box_len, edges_kf, n_mu=10, n_t=10, rsd=False, beta=0.0,
-                 precision="fp32", stream=None, autotune=False):
+                 precision="fp32", stream=None, autotune=False, k1_merge=1,
+                 label_k="shell"):
         self._edges = np.ascontiguousarray(np.asarray(edges_kf, dtype=np.float64))
         desc = PlanDesc()
         desc.ng = int(ng)
@@ -201,6 +205,10 @@ class Plan:
         desc.precision = PRECISIONS[precision]
         desc.mem_budget_bytes = 0
         desc.autotune = 1 if autotune else 0
+        desc.k1_merge = int(k1_merge)
+        if label_k not in ("shell", "triangle"):
+            raise ValueError("label_k must be 'shell' or 'triangle'")
+        desc.label_k = 0 if label_k == "shell" else 1
         self.handle = None
         self.handle = bsp_plan_create(desc, stream)
         self.ng, self.box_len, self.n_mu, self.n_t = int(ng), float(box_len), int(n_mu), int(n_t)
@@ -208,6 +216,8 @@ class Plan:
         self.real_dtype = torch.float64 if precision == "fp64" else torch.float32
         self.complex_dtype = torch.complex128 if precision == "fp64" else torch.complex64
         self.n_triplets, self.n_shells, self.field_bytes, self.device_bytes = bsp_plan_info(self.handle)
+        self.k1_merge = max(int(k1_merge), 1)
+        self.n_groups = (self.n_shells + self.k1_merge - 1) // self.k1_merge
         self.triplets = bsp_plan_triplets(self.handle)
         self.ng_eval = bsp_plan_grid(self.handle)
         self.tuning = bsp_plan_tuning(self.handle)
@@ -234,11 +244,11 @@ class Plan:
                              f"{self.spec_shape()}")
 
     def estimate(self, spec: torch.Tensor, stream=None, with_grid=True):
-        """(b_triplet [n_triplets], b_grid [Ns, n_mu, n_t]) as float64 CUDA tensors."""
+        """(b_triplet [n_triplets], b_grid [n_groups, n_mu, n_t]) as float64 CUDA tensors."""
         self._check_spec(spec)
         dev = spec.device
         b = torch.empty(self.n_triplets, dtype=torch.float64, device=dev)
-        g = torch.empty((self.n_shells, self.n_mu, self.n_t), dtype=torch.float64, device=dev) \
+        g = torch.empty((self.n_groups, self.n_mu, self.n_t), dtype=torch.float64, device=dev) \
             if with_grid else None
         bsp_estimate(self.handle, spec, b, g, stream)
         return b, g
@@ -246,7 +256,7 @@ class Plan:
     def estimate_host(self, spec_host, stream=None):
         """Host-in, host-out estimate (copies inside the call). spec_host: pinned torch or numpy."""
         b = np.empty(self.n_triplets, dtype=np.float64)
-        g = np.empty((self.n_shells, self.n_mu, self.n_t), dtype=np.float64)
+        g = np.empty((self.n_groups, self.n_mu, self.n_t), dtype=np.float64)
         bsp_estimate_host(self.handle, spec_host, b, g, stream)
         return b, g
 

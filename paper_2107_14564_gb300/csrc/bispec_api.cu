@@ -110,6 +110,8 @@ struct bsp_plan {
   // description
   int ng = 0, ns = 0, n_mu = 0, n_t = 0, rsd = 0, prec = 0;
   int autotune = 0;
+  int k1_merge = 1;         // k1 shells per (mu, t) cell group
+  int label_k = BSP_LABEL_SHELL_MEAN;
   int ngs = 0;              // side of the evaluation grid (<= ng), see choose_eval_grid
   double sum_scale = 1.0;   // (ng / ngs)^3: sums over the ng^3 grid from sums over ngs^3
   double box_len = 0.0, beta = 0.0;
@@ -178,7 +180,8 @@ struct bsp_plan {
 
   size_t elem() const { return prec == BSP_FP64 ? sizeof(double) : sizeof(float); }
   long long nvox() const { return (long long)ngs * ngs * ngs; }  // voxels of the evaluation grid
-  int n_cells() const { return ns * n_mu * n_t; }
+  int n_groups() const { return (ns + k1_merge - 1) / k1_merge; }
+  int n_cells() const { return n_groups() * n_mu * n_t; }
   size_t spec_bytes() const { return (size_t)ng * ng * (ng / 2 + 1) * 2 * elem(); }
   size_t field_bytes() const { return (size_t)ns * (size_t)nvox() * elem(); }
 };
@@ -336,9 +339,10 @@ int assign_tc_rows(const std::vector<int2>& pairs, std::vector<int>& row_of, std
 template <typename T>
 bsp_status run_passes(const bsp_plan* p, const void* spec, int rsd, void* tw, void* g1, void* g2,
                       void* fields, const Item* xi, int nxi, const Item* yi, int nyi, const Item* zi,
-                      int nzi, int lines_xy, int lines_z, cudaStream_t s) {
+                      int nzi, int lines_xy, int lines_z, cudaStream_t s, int kweight = 0) {
   PassArgs a{};
   a.n_sm = p->n_sm;
+  a.kweight = kweight;
   a.spec = spec;
   a.g1 = g1;
   a.g2 = g2;
@@ -386,6 +390,9 @@ bsp_status validate(const bsp_plan_desc* d) {
     if (!isfinite(d->edges_kf[i]) || d->edges_kf[i] < 0.0) return fail(BSP_ERR_INVALID_ARG, "bad edge");
   for (int i = 0; i < d->n_shells; ++i)
     if (!(d->edges_kf[i + 1] > d->edges_kf[i])) return fail(BSP_ERR_INVALID_ARG, "edges must increase");
+  if (d->k1_merge < 0) return fail(BSP_ERR_INVALID_ARG, "k1_merge must be >= 0");
+  if (d->label_k != BSP_LABEL_SHELL_MEAN && d->label_k != BSP_LABEL_TRIANGLE_MEAN)
+    return fail(BSP_ERR_INVALID_ARG, "label_k must be a bsp_label_k");
   if (d->n_mu < 1 || d->n_t < 1 || d->n_mu > 4096 || d->n_t > 4096)
     return fail(BSP_ERR_INVALID_ARG, "n_mu and n_t must be >= 1");
   if (d->precision < BSP_FP64 || d->precision > BSP_MIXED_BF16X3)
@@ -438,6 +445,8 @@ bsp_status host_plan(bsp_plan* p, const bsp_plan_desc* d) {
   p->beta = d->rsd ? d->beta : 0.0;
   p->prec = d->precision;
   p->autotune = d->autotune;
+  p->k1_merge = d->k1_merge > 1 ? d->k1_merge : 1;
+  p->label_k = d->label_k;
   p->box_len = d->box_len;
   p->edges.assign(d->edges_kf, d->edges_kf + d->n_shells + 1);
   p->q.resize(p->ns + 1);
@@ -720,9 +729,14 @@ bsp_status build_levels(bsp_plan* p, cudaStream_t s) {
   return BSP_OK;
 }
 
-// Eq. (2.10) in FP64 on the GPU for the candidate bins: T_abc = sum_x i_a i_b i_c.
-bsp_status count_triangles(bsp_plan* p, const std::vector<int>& ca, const std::vector<int>& cb,
-                           const std::vector<int>& cc, std::vector<double>& tsum, cudaStream_t s) {
+// FP64 sums over the evaluation grid (unscaled) of products of three counting fields, Eq. (2.10):
+// indices n < ns name i_n of Eq. (2.11); with `lengths`, indices ns + n name the length-weighted
+// counting field w_n = sum_{k in n} |k| e^{i k.x} (|k| in units of k_f). Triplets that share
+// their first two indices should be adjacent. out[ids ? ids[t] : t] = the sum of triplet t.
+bsp_status plan_sums(bsp_plan* p, bool lengths, const std::vector<int>& ca, const std::vector<int>& cb,
+                     const std::vector<int>& cc, const std::vector<int>* ids, std::vector<double>& tsum,
+                     cudaStream_t s) {
+  const int nf = lengths ? 2 * p->ns : p->ns;
   const int lxy = fft_lines_for(p->ngs, BSP_FP64);
   const int lz = fft_lines_for(p->ngs / 2, BSP_FP64);
   std::vector<Item> xi, yi, zi;
@@ -739,17 +753,20 @@ bsp_status count_triangles(bsp_plan* p, const std::vector<int>& ca, const std::v
   TRY(dev_alloc(p, p->ngs * sizeof(double2), &tw)); tmp.push_back(tw);
   TRY(dev_alloc(p, g1_elems(p) * sizeof(double2), &g1)); tmp.push_back(g1);
   TRY(dev_alloc(p, g2_elems(p) * sizeof(double2), &g2)); tmp.push_back(g2);
-  TRY(dev_alloc(p, (size_t)p->ns * p->nvox() * sizeof(double), &f)); tmp.push_back(f);
+  TRY(dev_alloc(p, (size_t)nf * p->nvox() * sizeof(double), &f)); tmp.push_back(f);
   TRY(dev_upload(p, xi, &dxi, s)); tmp.push_back(dxi);
   TRY(dev_upload(p, yi, &dyi, s)); tmp.push_back(dyi);
   TRY(dev_upload(p, zi, &dzi, s)); tmp.push_back(dzi);
   TRY(launch_twiddles<double>(tw, p->ngs, s));
   TRY(run_passes<double>(p, nullptr, 0, tw, g1, g2, f, dxi, (int)xi.size(), dyi, (int)yi.size(), dzi,
                          (int)zi.size(), lxy, lz, s));
+  if (lengths)
+    TRY(run_passes<double>(p, nullptr, 0, tw, g1, g2, static_cast<double*>(f) + (size_t)p->ns * p->nvox(),
+                           dxi, (int)xi.size(), dyi, (int)yi.size(), dzi, (int)zi.size(), lxy, lz, s, 1));
   std::vector<int2> pairs;
   std::vector<Tile> tiles;
   std::vector<int> map;
-  make_tiles(ca, cb, cc, pairs, tiles, map);
+  make_tiles(ca, cb, cc, pairs, tiles, map, ids);
   Tile* dt = nullptr; int2* dp = nullptr; int* dm = nullptr;
   TRY(dev_upload(p, tiles, &dt, s)); tmp.push_back(dt);
   TRY(dev_upload(p, pairs, &dp, s)); tmp.push_back(dp);
@@ -757,7 +774,7 @@ bsp_status count_triangles(bsp_plan* p, const std::vector<int>& ca, const std::v
   ContractArgs c{};
   c.fields = f;
   c.nvox = p->nvox();
-  c.ns = p->ns;
+  c.ns = nf;
   c.tiles = dt;
   c.pairs = dp;
   c.tile_map = dm;
@@ -1132,7 +1149,7 @@ bsp_status bsp_plan_create(const bsp_plan_desc* desc, void* stream, bsp_plan** o
   st = dev_upload(p, p->geom, &p->d_geom, s);
   if (st != BSP_OK) { bsp_plan_destroy(p); return st; }
   std::vector<double> tsum;
-  st = count_triangles(p, ca, cb, cc, tsum, s);
+  st = plan_sums(p, false, ca, cb, cc, nullptr, tsum, s);
   if (st != BSP_OK) { bsp_plan_destroy(p); return st; }
   for (double& t : tsum) t *= p->sum_scale;  // sums over the ng^3 grid (exact up to rounding)
   const double ng3 = (double)p->ng * (double)p->ng * (double)p->ng;
@@ -1153,8 +1170,39 @@ bsp_status bsp_plan_create(const bsp_plan_desc* desc, void* stream, bsp_plan** o
     t.a = ca[i]; t.b = cb[i]; t.c = cc[i];
     t.ntri = rn;
     t.tsum = tsum[i];
-    const double k1 = p->kbar[t.a], k2 = p->kbar[t.b], k3 = p->kbar[t.c];
-    t.k1 = k1; t.k2 = k2; t.k3 = k3;
+    t.k1 = p->kbar[t.a]; t.k2 = p->kbar[t.b]; t.k3 = p->kbar[t.c];
+    p->trips.push_back(t);
+  }
+  if (p->label_k == BSP_LABEL_TRIANGLE_MEAN && !p->trips.empty()) {
+    // mean side lengths over each bin's triangles: sum w_a i_b i_c / sum i_a i_b i_c and the
+    // other two placements of w, with the count itself in the same launch (4 sums per bin)
+    struct E { int a, b, c, id; };
+    std::vector<E> ent;
+    const int ns = p->ns;
+    for (size_t i = 0; i < p->trips.size(); ++i) {
+      const bsp_triplet& t = p->trips[i];
+      const int id = 4 * (int)i;
+      ent.push_back({ns + t.a, t.b, t.c, id});
+      ent.push_back({t.a, ns + t.b, t.c, id + 1});
+      ent.push_back({t.a, t.b, ns + t.c, id + 2});
+      ent.push_back({t.a, t.b, t.c, id + 3});
+    }
+    std::sort(ent.begin(), ent.end(), [](const E& x, const E& y) {
+      return x.a != y.a ? x.a < y.a : x.b != y.b ? x.b < y.b : x.c < y.c;
+    });
+    std::vector<int> ea, eb, ec, eid;
+    for (const E& x : ent) { ea.push_back(x.a); eb.push_back(x.b); ec.push_back(x.c); eid.push_back(x.id); }
+    std::vector<double> ks;
+    st = plan_sums(p, true, ea, eb, ec, &eid, ks, s);
+    if (st != BSP_OK) { bsp_plan_destroy(p); return st; }
+    for (size_t i = 0; i < p->trips.size(); ++i) {
+      bsp_triplet& t = p->trips[i];
+      const double tt = ks[4 * i + 3];
+      t.k1 = ks[4 * i] / tt; t.k2 = ks[4 * i + 1] / tt; t.k3 = ks[4 * i + 2] / tt;
+    }
+  }
+  for (bsp_triplet& t : p->trips) {  // Eq. (2.4) and the (mu, t) cell
+    const double k1 = t.k1, k2 = t.k2, k3 = t.k3;
     t.t = k2 / k1;
     t.mu = 0.5 * (k1 / k2 + k2 / k1 - (k3 / k1) * (k3 / k2));
     const double mc = std::min(std::max(t.mu, 0.5), 1.0);
@@ -1162,7 +1210,6 @@ bsp_status bsp_plan_create(const bsp_plan_desc* desc, void* stream, bsp_plan** o
     t.i_mu = std::min((int)floor((mc - 0.5) * (2.0 * p->n_mu)), p->n_mu - 1);
     t.i_t = std::min((int)floor((tc - 0.5) * (2.0 * p->n_t)), p->n_t - 1);
     t.inside = (t.t >= 0.5 && t.t <= 1.0 && t.mu >= 0.5 && t.mu <= 1.0 && 2.0 * t.mu * t.t >= 1.0) ? 1 : 0;
-    p->trips.push_back(t);
   }
   // estimator buffers in the plan's precision
   p->lines_xy = fft_lines_for(p->ngs, p->prec);
@@ -1176,7 +1223,7 @@ bsp_status bsp_plan_create(const bsp_plan_desc* desc, void* stream, bsp_plan** o
     std::vector<std::vector<int>> cells(p->n_cells());
     for (size_t t = 0; t < p->trips.size(); ++t) {
       const bsp_triplet& b = p->trips[t];
-      cells[(b.a * p->n_mu + b.i_mu) * p->n_t + b.i_t].push_back((int)t);
+      cells[((b.a / p->k1_merge) * p->n_mu + b.i_mu) * p->n_t + b.i_t].push_back((int)t);
     }
     for (int c = 0; c < p->n_cells(); ++c) {
       cptr[c + 1] = cptr[c] + (int)cells[c].size();

@@ -113,7 +113,8 @@ __global__ void __launch_bounds__(kFftThreads) xpass_kernel(PassArgs a, int max_
     const int q = mx * mx + ky * ky + kz * kz;
     if (q >= g.qlo && q < g.qhi) {
       const int ix = mx < 0 ? mx + ng : mx;
-      C val = spec ? spec[((long long)ix * ng + iy) * hz + kz] : c_make<C>(T(1), T(0));
+      C val = spec ? spec[((long long)ix * ng + iy) * hz + kz]
+                   : c_make<C>(a.kweight ? T(sqrt((double)q)) : T(1), T(0));
       if (a.rsd) {
         const T fac = T(1.0 + a.beta * (double)(kz * kz) / (double)q);
         val = c_scale(val, fac);

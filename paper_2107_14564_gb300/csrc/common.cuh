@@ -73,6 +73,7 @@ struct PassArgs {
   int ngs;                // side of the evaluation grid (transform length), <= ng
   int rsd;
   double beta;
+  int kweight;            // generic X pass, counting input only: mode value |k| / k_f instead of 1
   FftStages st;           // stage list of this pass's line length
   int rmax;               // largest r of all shells
   int n_sm;               // SMs of the device (grid size of the persistent warp kernels)

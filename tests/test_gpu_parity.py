@@ -300,3 +300,54 @@ def test_shell_count_limits(lib):
     gp = lib.Plan(ng, float(ng), np.linspace(1.0, 64.0, 65), precision="mixed_bf16x3")
     assert gp.n_shells == 64
     gp.close()
+
+
+@pytest.mark.parametrize("k1_merge", [2, 3])
+def test_merged_k1_groups(lib, k1_merge):
+    """(mu, t) cells spanning k1_merge neighbouring k1 shells (Sec. 2.1, merging adjacent bins),
+    FP64 plan, device and host entries: grid shape, empty cells and values against the oracle."""
+    ng = 32
+    edges = _edges(ng, 8)
+    spec = _spec(ng, 2.0, 0.1, 41, c64=False)
+    pl = P.make_plan(ng, float(ng), edges, 6, 6, k1_merge=k1_merge)
+    res = fbe.estimate(spec, pl)
+    gp = lib.Plan(ng, float(ng), edges, 6, 6, precision="fp64", k1_merge=k1_merge)
+    assert gp.n_groups == pl.n_groups == -(-8 // k1_merge)
+    b, g = gp.estimate(torch.from_numpy(spec).cuda())
+    _, gh = gp.estimate_host(spec)
+    for grid in (g.cpu().numpy(), gh):
+        assert grid.shape == res["grid"].shape
+        assert np.array_equal(np.isnan(grid), np.isnan(res["grid"]))
+        ok = ~np.isnan(grid)
+        assert np.max(np.abs(grid[ok] - res["grid"][ok]) / np.abs(res["grid"][ok])) < 1e-10
+    assert np.max(np.abs(b.cpu().numpy() - res["b"]) / np.abs(res["b"])) < 1e-10
+
+
+def test_triangle_mean_labels(lib):
+    """label_k = 'triangle' (the bin's average triangle, Sec. 2.1): the plan's side lengths are
+    FP64 sums of Eq. (2.10) with one |k|-weighted counting field; against the oracle's to 1e-12,
+    (mu, t) and cells from them, and the bin values unchanged by the choice of labels."""
+    ng = 32
+    edges = _edges(ng, 8)
+    spec = _spec(ng, 2.0, 0.1, 43, c64=False)
+    pl = P.make_plan(ng, float(ng), edges, 10, 10, label_k="triangle")
+    res = fbe.estimate(spec, pl)
+    gp = lib.Plan(ng, float(ng), edges, 10, 10, precision="fp64", label_k="triangle")
+    tr = gp.triplets
+    assert [(int(a), int(b), int(c)) for a, b, c in zip(tr["a"], tr["b"], tr["c"])] == res["triplets"]
+    labs = res["labels"]
+    for k in ("k1", "k2", "k3", "mu", "t"):
+        want = np.array([l[k] for l in labs])
+        assert np.max(np.abs(tr[k] - want) / np.abs(want)) < 1e-12, k
+    # cells agree wherever the label is not within rounding of a cell edge
+    for k, n, cell in (("mu", 10, "i_mu"), ("t", 10, "i_t")):
+        want = np.array([l[k] for l in labs])
+        frac = (np.clip(want, 0.5, 1.0) - 0.5) * 2 * n
+        clear = np.abs(frac - np.rint(frac)) > 1e-9
+        assert np.array_equal(tr[cell][clear], np.array([l[cell] for l in labs])[clear])
+    shell = lib.Plan(ng, float(ng), edges, 10, 10, precision="fp64")
+    assert np.any(np.abs(shell.triplets["mu"] - tr["mu"]) > 1e-3)
+    b, _ = gp.estimate(torch.from_numpy(spec).cuda())
+    b0, _ = shell.estimate(torch.from_numpy(spec).cuda())
+    assert np.array_equal(b.cpu().numpy(), b0.cpu().numpy())
+    assert np.max(np.abs(b.cpu().numpy() - res["b"]) / np.abs(res["b"])) < 1e-10

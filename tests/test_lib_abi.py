@@ -37,12 +37,13 @@ def test_every_declared_symbol_is_exported(lib):
     assert set(names) == set(_lib.SIGNATURES)
 
 
-def _desc(lib_mod, edges, ng=32, prec=1, n_mu=10, n_t=10, rsd=0, beta=0.0):
+def _desc(lib_mod, edges, ng=32, prec=1, n_mu=10, n_t=10, rsd=0, beta=0.0, k1_merge=1, label_k=0):
     e = np.ascontiguousarray(edges, dtype=np.float64)
     d = lib_mod.PlanDesc()
     d.ng, d.box_len, d.n_shells = ng, float(ng), len(e) - 1
     d.edges_kf = e.ctypes.data_as(C.POINTER(C.c_double))
     d.n_mu, d.n_t, d.rsd, d.beta, d.precision, d.mem_budget_bytes = n_mu, n_t, rsd, beta, prec, 0
+    d.k1_merge, d.label_k = k1_merge, label_k
     return d, e
 
 
@@ -54,6 +55,8 @@ def _desc(lib_mod, edges, ng=32, prec=1, n_mu=10, n_t=10, rsd=0, beta=0.0):
     (dict(edges=[1.5, 1.6]), 1),                    # empty shell: ceil(2.25) == ceil(2.56)
     (dict(edges=[1.0, 3.0], prec=9), 1),
     (dict(edges=[1.0, 3.0], n_mu=0), 1),
+    (dict(edges=[1.0, 3.0], k1_merge=-1), 1),
+    (dict(edges=[1.0, 3.0], label_k=2), 1),
 ])
 def test_argument_errors_without_gpu(lib, kw, status):
     from paper_2107_14564_gb300 import _lib
@@ -72,3 +75,18 @@ def test_null_arguments(lib):
 
 def test_version(lib):
     assert b"sm_103a" in lib.bsp_version()
+
+
+def test_plan_desc_layout_matches_the_header():
+    """The binding's PlanDesc lists the fields of bsp_plan_desc in the header's order."""
+    from paper_2107_14564_gb300 import _lib
+    txt = open(os.path.join(ROOT, "include", "bispec.h")).read()
+    body = re.search(r"typedef struct \{(.*?)\} bsp_plan_desc;", txt, flags=re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    names = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if decl:
+            names += [re.sub(r"[\s\*]", "", n.split()[-1] if i == 0 else n)
+                      for i, n in enumerate(decl.split(","))]
+    assert names == [f[0] for f in _lib.PlanDesc._fields_]

@@ -182,3 +182,77 @@ def test_fields_on_a_coarser_grid():
     small = fbe.shell_fields_on_grid(spec, pl, 16)
     bad = fbe.triple_sums(small, trips) * (ng / 16) ** 3
     assert np.max(np.abs(bad - want) / np.abs(want)) > 1e-3
+
+
+@pytest.mark.parametrize("k1_merge,n_mu,n_t", [(1, 4, 4), (3, 4, 4), (8, 1, 1)])
+def test_merged_cells_are_bigger_bins_summed_mode_by_mode(k1_merge, n_mu, n_t):
+    """The (mu, t) grid (Sec. 2.1, merging adjacent bins): every cell is one bigger bin of
+    Eq. (2.3), here built from the direct mode sums of Eq. (2.9) over the triangles of its member
+    bins (k1 shell a with a // k1_merge = group, labels in the cell), divided by their direct
+    triangle count. k1_merge = Ns with one (mu, t) cell merges every bin into one number."""
+    ng = 16
+    pl = _plan(ng, k1_merge=k1_merge, n_mu=n_mu, n_t=n_t)
+    spec = fieldgen.spectrum(fieldgen.quadratic_field(ng, float(ng), 2.0, 0.2, 31))
+    res = fbe.estimate(spec, pl)
+    msum_d, ntri_d = dbe.direct_estimate(spec, pl)
+    num = np.zeros((pl.n_groups, n_mu, n_t))
+    den = np.zeros((pl.n_groups, n_mu, n_t))
+    for t in res["triplets"]:
+        k = [pl.kbar[s] for s in t]
+        mu, tt = P.shape_label(*k)
+        im, it = P.shape_cell(mu, tt, n_mu, n_t)
+        num[t[0] // k1_merge, im, it] += msum_d[t].real
+        den[t[0] // k1_merge, im, it] += ntri_d[t]
+    want = np.full(num.shape, np.nan)
+    ok = den > 0
+    want[ok] = pl.vcell ** 3 / pl.volume * num[ok] / den[ok]
+    got = res["grid"]
+    assert got.shape == (-(-pl.ns // k1_merge), n_mu, n_t)
+    assert np.array_equal(np.isnan(got), ~ok)
+    assert np.max(np.abs(got[ok] - want[ok]) / np.abs(want[ok])) < 1e-10
+    if k1_merge == pl.ns:
+        assert got.shape == (1, 1, 1)
+
+
+@pytest.mark.parametrize("ng", [16, 32])
+def test_triangle_mean_lengths_equal_mode_by_mode_means(ng):
+    """Labels from each bin's average triangle (Sec. 2.1): the FFT sums with length-weighted
+    counting fields equal the means of |k_a|, |k_b|, |k_c| over the triangles enumerated one by
+    one; each mean lies inside its shell, and two equal shells give equal means (symmetry)."""
+    pl = _plan(ng, label_k="triangle")
+    trips, _, _ = fbe.kept_triplets(pl)
+    got = fbe.triangle_mean_k(pl, trips)
+    want = dbe.direct_mean_k(pl)
+    assert set(want) == set(trips)
+    for i, t in enumerate(trips):
+        assert np.all(np.abs(got[i] - want[t]) <= 1e-12 * np.asarray(want[t]))
+        for j, s in enumerate(t):
+            assert np.sqrt(pl.thresholds[s]) - 1e-12 <= got[i, j] < np.sqrt(pl.thresholds[s + 1])
+        if t[0] == t[1]:
+            assert abs(got[i, 0] - got[i, 1]) <= 1e-12 * got[i, 0]
+        if t[1] == t[2]:
+            assert abs(got[i, 1] - got[i, 2]) <= 1e-12 * got[i, 1]
+
+
+def test_triangle_labels_in_the_estimate():
+    """With label_k = 'triangle' the estimate's labels come from the bins' mean triangles, the
+    values B are unchanged, and on one-radius shells (every mode of a shell has the same |k|)
+    both label choices coincide."""
+    ng = 16
+    spec = fieldgen.spectrum(fieldgen.quadratic_field(ng, float(ng), 2.0, 0.2, 33))
+    shell = fbe.estimate(spec, _plan(ng))
+    tri = fbe.estimate(spec, _plan(ng, label_k="triangle"))
+    assert np.array_equal(shell["b"], tri["b"])
+    km = fbe.triangle_mean_k(_plan(ng), tri["triplets"])
+    assert [l["k1"] for l in tri["labels"]] == list(km[:, 0])
+    assert any(abs(l1["mu"] - l2["mu"]) > 1e-3 for l1, l2 in zip(shell["labels"], tri["labels"]))
+    # shells of one radius each: |m|^2 = 9 .. 26 (15 and 23 are no sums of three squares and
+    # join the shell below); every triangle of a bin then has the shells' lengths
+    qs = [q for q in range(9, 28) if q not in (15, 23)]
+    pl1 = P.make_plan(ng, float(ng), np.sqrt(np.array(qs, dtype=float)) - 1e-9, label_k="triangle")
+    assert list(pl1.thresholds) == qs
+    one = fbe.estimate(spec, pl1)
+    for (a, b, c), lab in zip(one["triplets"], one["labels"]):
+        want = np.sqrt([pl1.thresholds[a], pl1.thresholds[b], pl1.thresholds[c]])
+        assert np.all(np.abs(np.array([lab["k1"], lab["k2"], lab["k3"]]) - want) <= 1e-12 * want)
+        assert np.allclose(want, pl1.kbar[[a, b, c]], rtol=1e-15, atol=0)
