@@ -44,6 +44,10 @@ WORKLOADS["prof256"] = dict(ng=256, box=256.0, n_index=1.5, f_ng=0.05, beta=None
                             n_mu=10, n_t=10, seed=12,
                             text="profiling case: Ng=256 L=256, 32 linear shells k_f..k_Nyq/2, 10x10 cells "
                                  "(full 128-row tensor-core tiles on a 256^3 grid, 2 GB of fields)")
+WORKLOADS["ng768"] = dict(ng=768, box=768.0, n_index=1.5, f_ng=0.05, beta=None, ns=24, top=192.0,
+                          n_mu=20, n_t=20, seed=7,
+                          text="forward-only Ng=768 L=768 quadratic NG field P=k^-1.5 f=0.05, 24 linear shells "
+                               "k_f..k_Nyq/2, 20x20 (mu,t) cells (run FP32, optionally under --mem-budget-gb)")
 WORKLOADS["batch64"] = dict(text="64 seeded quadratic NG fields (P=k^-1.5, f=0.05) on uneven grids: 16 x 128^3, "
                                  "24 x 192^3, 24 x 256^3 (L=Ng), 16 linear shells k_f..k_Nyq/2 each, 10x10 "
                                  "(mu,t) cells, one captured CUDA graph",
@@ -250,10 +254,10 @@ def run_ours(args, w):
     t0 = time.perf_counter()
     plan = binding.Plan(w["ng"], w["box"], edges_of(w), w["n_mu"], w["n_t"],
                         rsd=w["beta"] is not None, beta=w["beta"] or 0.0, precision=args.precision,
-                        autotune=not args.no_autotune)
+                        autotune=not args.no_autotune, mem_budget_bytes=int(args.mem_budget_gb * 2 ** 30))
     plan_s = time.perf_counter() - t0
     log(f"[bench] plan: {plan.n_triplets} bins, {plan.device_bytes / 1e9:.1f} GB on device, "
-        f"{plan_s:.1f} s")
+        f"{plan_s:.1f} s, x-slabs {plan.slabs}")
     for _ in range(args.warmup):
         plan.estimate(spec)
     torch.cuda.synchronize()
@@ -387,7 +391,8 @@ def run_ours(args, w):
             "fields_per_sec": fields_per_s, "n_bins": plan.n_triplets, "roofline": roof,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(nlaunch.value), "clocks": clk,
             "stages": stages, "plan_seconds": round(plan_s, 2), "plain_fp32": plain,
-            "eval_grid": plan.ng_eval, "contraction_levels": plan.tuning}
+            "eval_grid": plan.ng_eval, "contraction_levels": plan.tuning,
+            "device_bytes": plan.device_bytes, "x_slabs": list(plan.slabs)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     plan.close()
@@ -460,6 +465,8 @@ def main():
                     help="skip timing the plain FP32 (CUDA-core contraction) form beside the main one")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="ng512_rsd")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mem-budget-gb", type=float, default=0.0,
+                    help="GiB of shell fields a plan may hold (0: all); FP32/FP64 plans then stream x-slabs")
     ap.add_argument("--no-autotune", action="store_true",
                     help="plans skip the contraction autotuner (fixed split: one voxel block per SM)")
     args = ap.parse_args()

@@ -80,7 +80,17 @@ typedef struct {
   int rsd;                 /* 1: multiply the spectrum by 1 + beta (k_z/|k|)^2 (Eq. (3.4)) */
   double beta;             /* linear RSD parameter beta_1 of Eq. (3.4) */
   int precision;           /* a bsp_precision */
-  size_t mem_budget_bytes; /* reserved, 0 */
+  size_t mem_budget_bytes; /* 0: hold every shell field of an estimate at once (N_s S^3 reals on the
+                              evaluation grid of side S, bsp_plan_grid). Otherwise the most bytes of
+                              shell fields the plan may hold: when the fields exceed it, estimates,
+                              plan-time counts and bsp_grad make the X and Y passes once and then
+                              produce and reduce the fields one x-slab of the evaluation grid at a
+                              time (the largest slab within the budget, sums added in FP64), on one
+                              contraction level. The X/Y pass buffers are outside the budget. A
+                              budget below one x-plane of all shells is BSP_ERR_INVALID_ARG;
+                              BSP_MIXED_BF16X3 plans whose fields exceed it are
+                              BSP_ERR_NOT_SUPPORTED. Results equal the unbudgeted plan's up to the
+                              order of the sums. */
   int autotune;            /* 1: at creation, time the tensor-core contraction of every level with
                               its voxels split over 1, 2 and 4 x (SM count) blocks per M tile and
                               keep the fastest (BSP_MIXED_BF16X3 plans; the split changes only the
@@ -226,7 +236,8 @@ BSP_API bsp_status bsp_plan_check(bsp_plan* plan, void* stream);
 enum {
   BSP_STAGE_XPASS = 0,    /* shell-masked C2C along x (Eq. (2.8)) */
   BSP_STAGE_YPASS = 1,    /* C2C along y */
-  BSP_STAGE_ZPASS = 2,    /* C2R along z: the shell fields d_n(x) */
+  BSP_STAGE_ZPASS = 2,    /* C2R along z: the shell fields d_n(x) (with x-slabs: every slab's Z pass
+                             and contraction) */
   BSP_STAGE_CONTRACT = 3, /* triple products sum_x d_a d_b d_c (Eq. (2.7) numerator) */
   BSP_STAGE_FINALIZE = 4, /* cross-block sums, B = V_c^3 M / (V T) and the (mu, t) cells */
   BSP_N_STAGES = 5
@@ -252,6 +263,11 @@ BSP_API bsp_status bsp_plan_stage_work(const bsp_plan* plan, double* bytes, doub
 
 /* Bytes bsp_estimate_host copies host->device per call (the spectrum box of the outermost shell). */
 BSP_API bsp_status bsp_plan_host_input_bytes(const bsp_plan* plan, size_t* bytes);
+
+/* The x-slabs an estimate streams under mem_budget_bytes: slab_planes x-planes of the evaluation
+ * grid per slab (the last one may be thinner) and n_slabs of them; 0 and 1 when the plan holds
+ * all fields at once. */
+BSP_API bsp_status bsp_plan_slabs(const bsp_plan* plan, int* slab_planes, int* n_slabs);
 
 /* Limits of bsp_triple_sums_noalloc (its scratch array has a fixed size). */
 #define BSP_NOALLOC_MAX_TRIPLETS 4096

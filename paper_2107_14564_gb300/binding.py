@@ -52,6 +52,13 @@ def bsp_plan_grid(handle) -> int:
     return n.value
 
 
+def bsp_plan_slabs(handle):
+    """(x-planes per slab, number of slabs) an estimate streams; (0, 1) without a memory budget."""
+    planes, n = C.c_int(), C.c_int()
+    check(_lib.load().bsp_plan_slabs(handle, C.byref(planes), C.byref(n)))
+    return planes.value, n.value
+
+
 def bsp_plan_host_input_bytes(handle) -> int:
     n = C.c_size_t(0)
     check(_lib.load().bsp_plan_host_input_bytes(handle, C.byref(n)))
@@ -187,11 +194,12 @@ class Plan:
     per level at creation and keep the fastest (tensor-core plans); k1_merge: (mu, t) cells span
     this many neighbouring k1 shells (b_grid has ceil(Ns / k1_merge) groups); label_k: 'shell'
     forms (mu, t) from the shells' mean |k|, 'triangle' from the mean sides of each bin's
-    triangles."""
+    triangles; mem_budget_bytes: the most bytes of shell fields to hold at once (0: all; else
+    fields are produced and reduced x-slab by x-slab, see .slabs)."""
 
     def __init__(self, ng, box_len, edges_kf, n_mu=10, n_t=10, rsd=False, beta=0.0,
                  precision="fp32", stream=None, autotune=False, k1_merge=1,
-                 label_k="shell"):
+                 label_k="shell", mem_budget_bytes=0):
         self._edges = np.ascontiguousarray(np.asarray(edges_kf, dtype=np.float64))
         desc = PlanDesc()
         desc.ng = int(ng)
@@ -203,7 +211,7 @@ class Plan:
         desc.rsd = 1 if rsd else 0
         desc.beta = float(beta)
         desc.precision = PRECISIONS[precision]
-        desc.mem_budget_bytes = 0
+        desc.mem_budget_bytes = int(mem_budget_bytes)
         desc.autotune = 1 if autotune else 0
         desc.k1_merge = int(k1_merge)
         if label_k not in ("shell", "triangle"):
@@ -222,6 +230,7 @@ class Plan:
         self.ng_eval = bsp_plan_grid(self.handle)
         self.tuning = bsp_plan_tuning(self.handle)
         self.host_input_bytes = bsp_plan_host_input_bytes(self.handle)
+        self.slabs = bsp_plan_slabs(self.handle)
 
     def close(self):
         if self.handle is not None:
@@ -300,5 +309,5 @@ class Plan:
 
 
 __all__ = ["Plan", "BispecError", "bsp_plan_create", "bsp_plan_destroy", "bsp_plan_info",
-           "bsp_plan_triplets", "bsp_plan_grid", "bsp_plan_tuning", "bsp_plan_host_input_bytes", "bsp_shell_fields", "bsp_contract", "bsp_estimate",
+           "bsp_plan_triplets", "bsp_plan_grid", "bsp_plan_tuning", "bsp_plan_host_input_bytes", "bsp_plan_slabs", "bsp_shell_fields", "bsp_contract", "bsp_estimate",
            "bsp_estimate_host", "bsp_estimate_batched", "Batch", "bsp_spectrum", "bsp_grad", "bsp_last_sums", "bsp_plan_check", "bsp_version", "TRIPLET_DTYPE"]

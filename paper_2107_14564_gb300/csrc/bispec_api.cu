@@ -112,6 +112,9 @@ struct bsp_plan {
   int autotune = 0;
   int k1_merge = 1;         // k1 shells per (mu, t) cell group
   int label_k = BSP_LABEL_SHELL_MEAN;
+  size_t mem_budget = 0;    // bytes of shell fields the plan may hold at once (0: no limit)
+  int slab_nx = 0;          // > 0: estimates stream x-slabs of this many planes of the evaluation grid
+  std::vector<int> zi_off;  // generic Z items of slab k: [zi_off[k], zi_off[k + 1])
   int ngs = 0;              // side of the evaluation grid (<= ng), see choose_eval_grid
   double sum_scale = 1.0;   // (ng / ngs)^3: sums over the ng^3 grid from sums over ngs^3
   double box_len = 0.0, beta = 0.0;
@@ -184,6 +187,10 @@ struct bsp_plan {
   int n_cells() const { return n_groups() * n_mu * n_t; }
   size_t spec_bytes() const { return (size_t)ng * ng * (ng / 2 + 1) * 2 * elem(); }
   size_t field_bytes() const { return (size_t)ns * (size_t)nvox() * elem(); }
+  int n_slabs() const { return slab_nx ? (ngs + slab_nx - 1) / slab_nx : 1; }
+  int slab_x0(int k) const { return k * slab_nx; }
+  int slab_len(int k) const { return slab_nx ? std::min(slab_nx, ngs - k * slab_nx) : ngs; }
+  size_t store_bytes() const { return (size_t)ns * (size_t)slab_len(0) * ngs * ngs * elem(); }  // p->fields
 };
 
 struct bsp_batch {
@@ -339,7 +346,8 @@ int assign_tc_rows(const std::vector<int2>& pairs, std::vector<int>& row_of, std
 template <typename T>
 bsp_status run_passes(const bsp_plan* p, const void* spec, int rsd, void* tw, void* g1, void* g2,
                       void* fields, const Item* xi, int nxi, const Item* yi, int nyi, const Item* zi,
-                      int nzi, int lines_xy, int lines_z, cudaStream_t s, int kweight = 0) {
+                      int nzi, int lines_xy, int lines_z, cudaStream_t s, int kweight = 0, bool do_xy = true,
+                      bool do_z = true, int slab_x0 = 0, int slab_nx = 0) {
   PassArgs a{};
   a.n_sm = p->n_sm;
   a.kweight = kweight;
@@ -353,15 +361,21 @@ bsp_status run_passes(const bsp_plan* p, const void* spec, int rsd, void* tw, vo
   a.ngs = p->ngs;
   a.rsd = rsd;
   a.beta = p->beta;
-  a.st = p->st_full;
-  a.items = xi;
-  bsp_status st = launch_xpass<T>(a, nxi, lines_xy, s);
-  if (st != BSP_OK) return st;
-  a.items = yi;
-  st = launch_ypass<T>(a, nyi, lines_xy, s);
-  if (st != BSP_OK) return st;
+  bsp_status st;
+  if (do_xy) {
+    a.st = p->st_full;
+    a.items = xi;
+    st = launch_xpass<T>(a, nxi, lines_xy, s);
+    if (st != BSP_OK) return st;
+    a.items = yi;
+    st = launch_ypass<T>(a, nyi, lines_xy, s);
+    if (st != BSP_OK) return st;
+  }
+  if (!do_z) return BSP_OK;
   a.items = zi;
   a.st = p->st_half;
+  a.slab_x0 = slab_x0;
+  a.slab_nx = slab_nx;
   return launch_zpass<T>(a, nzi, lines_z, s);
 }
 
@@ -505,7 +519,30 @@ bsp_status host_plan(bsp_plan* p, const bsp_plan_desc* d) {
     o1 += (long long)p->ngs * (2 * g.r - 1) * g.r;
     o2 += (long long)p->ngs * p->ngs * g.r;
   }
+  // memory budget: stream x-slabs of the evaluation grid when all fields do not fit
+  p->mem_budget = d->mem_budget_bytes;
+  if (p->mem_budget > 0 && p->mem_budget < p->field_bytes()) {
+    if (p->prec == BSP_MIXED_BF16X3)
+      return fail(BSP_ERR_NOT_SUPPORTED, "mem_budget_bytes below the shell fields of a split-BF16 plan");
+    const size_t plane = (size_t)p->ns * p->ngs * p->ngs * p->elem();
+    if (p->mem_budget < plane) return fail(BSP_ERR_INVALID_ARG, "mem_budget_bytes below one x-plane of all shell fields");
+    p->slab_nx = (int)std::min<size_t>(p->mem_budget / plane, (size_t)p->ngs - 1);
+  }
   return BSP_OK;
+}
+
+// Generic Z-pass items reordered slab by slab (x-slabs of slab_nx planes; one slab when 0), with
+// the start of each slab's range in off[k].
+void slab_items(int slab_nx, int grid, std::vector<Item>& zi, std::vector<int>& off) {
+  const int nsl = slab_nx ? (grid + slab_nx - 1) / slab_nx : 1;
+  std::vector<Item> out;
+  off.assign(nsl + 1, 0);
+  for (int k = 0; k < nsl; ++k) {
+    for (const Item& it : zi)
+      if (!slab_nx || it.u / slab_nx == k) out.push_back(it);
+    off[k + 1] = (int)out.size();
+  }
+  zi.swap(out);
 }
 
 long long g1_elems(const bsp_plan* p) {
@@ -594,7 +631,7 @@ bsp_status build_levels(bsp_plan* p, cudaStream_t s) {
     }
     const int need = p->geom[p->trips[t].a].r + p->geom[p->trips[t].b].r + p->geom[cmax].r - 2;
     int g = S;
-    for (int cand = 16; cand < S; cand += 8)
+    for (int cand = 16; cand < S && !p->slab_nx; cand += 8)  // x-slab plans: one level
       if (S % cand == 0 && cand >= need) { g = cand; break; }
     std::vector<int>& v = bins_of(g);
     for (size_t w = t; w < u; ++w) v.push_back((int)w);
@@ -737,32 +774,53 @@ bsp_status plan_sums(bsp_plan* p, bool lengths, const std::vector<int>& ca, cons
                      const std::vector<int>& cc, const std::vector<int>* ids, std::vector<double>& tsum,
                      cudaStream_t s) {
   const int nf = lengths ? 2 * p->ns : p->ns;
-  const int lxy = fft_lines_for(p->ngs, BSP_FP64);
-  const int lz = fft_lines_for(p->ngs / 2, BSP_FP64);
+  const int S = p->ngs;
+  const int lxy = fft_lines_for(S, BSP_FP64);
+  const int lz = fft_lines_for(S / 2, BSP_FP64);
   std::vector<Item> xi, yi, zi;
   make_items(p, lxy, lz, xi, yi, zi);
+  // under a memory budget the FP64 fields are produced and contracted one x-slab at a time
+  int nx = S;
+  if (p->mem_budget > 0) {
+    const size_t plane = (size_t)nf * S * S * sizeof(double);
+    nx = (int)std::max<size_t>(1, std::min<size_t>((size_t)S, p->mem_budget / plane));
+  }
+  const int slab = nx < S ? nx : 0;
+  std::vector<int> zoff;
+  slab_items(slab, S, zi, zoff);
+  const int nsl = (int)zoff.size() - 1;
+  const long long slab_vox = (long long)nx * S * S;
   std::vector<void*> tmp;
   auto cleanup = [&]() {
     cudaStreamSynchronize(s);
     for (void* d : tmp) dev_free(p, d);
   };
-  void *tw = nullptr, *g1 = nullptr, *g2 = nullptr, *f = nullptr;
+  void *tw = nullptr, *g1 = nullptr, *g2 = nullptr, *g2w = nullptr, *f = nullptr;
   Item *dxi = nullptr, *dyi = nullptr, *dzi = nullptr;
   bsp_status st;
 #define TRY(x) do { st = (x); if (st != BSP_OK) { cleanup(); return st; } } while (0)
-  TRY(dev_alloc(p, p->ngs * sizeof(double2), &tw)); tmp.push_back(tw);
+  TRY(dev_alloc(p, S * sizeof(double2), &tw)); tmp.push_back(tw);
   TRY(dev_alloc(p, g1_elems(p) * sizeof(double2), &g1)); tmp.push_back(g1);
   TRY(dev_alloc(p, g2_elems(p) * sizeof(double2), &g2)); tmp.push_back(g2);
-  TRY(dev_alloc(p, (size_t)nf * p->nvox() * sizeof(double), &f)); tmp.push_back(f);
+  if (slab && lengths) { TRY(dev_alloc(p, g2_elems(p) * sizeof(double2), &g2w)); tmp.push_back(g2w); }
+  TRY(dev_alloc(p, (size_t)nf * slab_vox * sizeof(double), &f)); tmp.push_back(f);
   TRY(dev_upload(p, xi, &dxi, s)); tmp.push_back(dxi);
   TRY(dev_upload(p, yi, &dyi, s)); tmp.push_back(dyi);
   TRY(dev_upload(p, zi, &dzi, s)); tmp.push_back(dzi);
-  TRY(launch_twiddles<double>(tw, p->ngs, s));
-  TRY(run_passes<double>(p, nullptr, 0, tw, g1, g2, f, dxi, (int)xi.size(), dyi, (int)yi.size(), dzi,
-                         (int)zi.size(), lxy, lz, s));
-  if (lengths)
-    TRY(run_passes<double>(p, nullptr, 0, tw, g1, g2, static_cast<double*>(f) + (size_t)p->ns * p->nvox(),
-                           dxi, (int)xi.size(), dyi, (int)yi.size(), dzi, (int)zi.size(), lxy, lz, s, 1));
+  TRY(launch_twiddles<double>(tw, S, s));
+  if (!slab) {
+    TRY(run_passes<double>(p, nullptr, 0, tw, g1, g2, f, dxi, (int)xi.size(), dyi, (int)yi.size(), dzi,
+                           (int)zi.size(), lxy, lz, s));
+    if (lengths)
+      TRY(run_passes<double>(p, nullptr, 0, tw, g1, g2, static_cast<double*>(f) + (size_t)p->ns * slab_vox,
+                             dxi, (int)xi.size(), dyi, (int)yi.size(), dzi, (int)zi.size(), lxy, lz, s, 1));
+  } else {
+    TRY(run_passes<double>(p, nullptr, 0, tw, g1, g2, f, dxi, (int)xi.size(), dyi, (int)yi.size(), dzi, 0, lxy,
+                           lz, s, 0, true, false));
+    if (lengths)
+      TRY(run_passes<double>(p, nullptr, 0, tw, g1, g2w, f, dxi, (int)xi.size(), dyi, (int)yi.size(), dzi, 0, lxy,
+                             lz, s, 1, true, false));
+  }
   std::vector<int2> pairs;
   std::vector<Tile> tiles;
   std::vector<int> map;
@@ -773,13 +831,13 @@ bsp_status plan_sums(bsp_plan* p, bool lengths, const std::vector<int>& ca, cons
   TRY(dev_upload(p, map, &dm, s)); tmp.push_back(dm);
   ContractArgs c{};
   c.fields = f;
-  c.nvox = p->nvox();
+  c.nvox = slab_vox;
   c.ns = nf;
   c.tiles = dt;
   c.pairs = dp;
   c.tile_map = dm;
   c.ntiles = (int)tiles.size();
-  c.gridx = pick_gridx(p, c.ntiles);
+  c.gridx = pick_gridx_n(p->n_sm, c.ntiles, slab_vox);
   void* part = nullptr; void* ms = nullptr;
   TRY(dev_alloc(p, (size_t)c.gridx * c.ntiles * 16 * sizeof(double), &part)); tmp.push_back(part);
   TRY(dev_alloc(p, ca.size() * sizeof(double), &ms)); tmp.push_back(ms);
@@ -787,8 +845,21 @@ bsp_status plan_sums(bsp_plan* p, bool lengths, const std::vector<int>& ca, cons
   c.msum = static_cast<double*>(ms);
   c.n_out = (int)ca.size();
   c.scale = 1.0;  // scaled to the ng^3 grid on the host
-  TRY(launch_contract_simt<double>(c, s));
-  TRY(launch_reduce_partials(c, s));
+  for (int k = 0; k < nsl; ++k) {
+    if (slab) {  // the slab's fields, [nf][x - x0][y][z]
+      const int x0 = k * nx, len = std::min(nx, S - x0);
+      const int nzk = zoff[k + 1] - zoff[k];
+      c.nvox = (long long)len * S * S;
+      TRY(run_passes<double>(p, nullptr, 0, tw, g1, g2, f, dxi, 0, dyi, 0, dzi + zoff[k], nzk, lxy, lz, s, 0, false,
+                             true, x0, len));
+      if (lengths)
+        TRY(run_passes<double>(p, nullptr, 0, tw, g1, g2w, static_cast<double*>(f) + (size_t)p->ns * c.nvox, dxi, 0,
+                               dyi, 0, dzi + zoff[k], nzk, lxy, lz, s, 1, false, true, x0, len));
+    }
+    c.accumulate = k > 0;
+    TRY(launch_contract_simt<double>(c, s));
+    TRY(launch_reduce_partials(c, s));
+  }
   tsum.assign(ca.size(), 0.0);
   cudaError_t e = cudaMemcpyAsync(tsum.data(), ms, ca.size() * sizeof(double), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -879,11 +950,42 @@ int contract_launches(const bsp_plan* p) {
   return n + (p->prec == BSP_MIXED_BF16X3 ? 1 : 0);  // one cross-block sum for all tensor-core levels
 }
 
-// The three pass launches of an estimate on the plan's buffers; ev (optional) receives an event
-// after the X and after the Y pass, and after the Z pass. split: write split fields (the layout
-// of the tensor-core contraction, see TcArgs) instead of FP32 ones.
+// The contraction of x-slab k of an x-slab plan (one level, the evaluation grid) on the slab's
+// fields in p->fields, its sums added to msum after the first slab.
 template <typename T>
-bsp_status plan_passes(bsp_plan* p, const void* spec, void* fields, cudaStream_t s, cudaEvent_t* ev, bool split = false) {
+bsp_status contract_slab(bsp_plan* p, int k, cudaStream_t s) {
+  if (p->levels.empty() || p->levels[0].ntiles == 0) return BSP_OK;
+  const ContractLevel& L = p->levels[0];
+  ContractArgs c{};
+  c.fields = p->fields;
+  c.nvox = (long long)p->slab_len(k) * p->ngs * p->ngs;
+  c.ns = p->ns;
+  c.tiles = L.d_tiles;
+  c.pairs = L.d_pairs;
+  c.tile_map = L.d_map;
+  c.ntiles = L.ntiles;
+  c.gridx = L.gridx;
+  c.partial = L.partial;
+  c.msum = p->msum;
+  c.n_out = (int)L.bins.size();
+  c.scale = L.scale;
+  c.accumulate = k > 0;
+  bsp_status st = launch_contract_simt<T>(c, s);
+  if (st != BSP_OK) return st;
+  return launch_reduce_partials(c, s);
+}
+
+// Which passes plan_passes launches: all three over the whole grid, the X and Y passes only, or
+// (a value k >= 0) the Z pass of x-slab k, its fields laid out [n][x - x0][y][z] in `fields`.
+constexpr int kPassAll = -1;
+constexpr int kPassXY = -2;
+
+// The pass launches of an estimate on the plan's buffers; ev (optional) receives an event after
+// the X and after the Y pass, and after the Z pass. split: write split fields (the layout of the
+// tensor-core contraction, see TcArgs) instead of FP32 ones.
+template <typename T>
+bsp_status plan_passes(bsp_plan* p, const void* spec, void* fields, cudaStream_t s, cudaEvent_t* ev, bool split = false,
+                       int part = kPassAll) {
   PassArgs a{};
   a.n_sm = p->n_sm;
   a.spec = spec;
@@ -907,39 +1009,58 @@ bsp_status plan_passes(bsp_plan* p, const void* spec, void* fields, cudaStream_t
       a.zmask = p->d_zmask;
       a.n_zlev = p->n_zlev;
     }
-    a.items = p->d_wxi;
-    st = launch_warp_xpass(a, p->nwxi, s);
+    if (part < 0) {
+      a.items = p->d_wxi;
+      st = launch_warp_xpass(a, p->nwxi, s);
+      if (st != BSP_OK) return st;
+      if (ev) BSP_CUDA(cudaEventRecord(ev[0], s));
+      a.items = p->d_wyi;
+      st = launch_warp_ypass(a, p->nwyi, s);
+      if (st != BSP_OK) return st;
+      if (ev) BSP_CUDA(cudaEventRecord(ev[1], s));
+      if (part == kPassXY) return BSP_OK;
+    }
+    long long lines = (long long)p->ns * p->ngs * p->ngs;
+    if (part >= 0) {
+      a.slab_x0 = p->slab_x0(part);
+      a.slab_nx = p->slab_len(part);
+      lines = (long long)p->ns * a.slab_nx * p->ngs;
+    }
+    st = launch_warp_zpass(a, lines, p->n_sm, s);
     if (st != BSP_OK) return st;
-    if (ev) BSP_CUDA(cudaEventRecord(ev[0], s));
-    a.items = p->d_wyi;
-    st = launch_warp_ypass(a, p->nwyi, s);
-    if (st != BSP_OK) return st;
-    if (ev) BSP_CUDA(cudaEventRecord(ev[1], s));
-    st = launch_warp_zpass(a, (long long)p->ns * p->ngs * p->ngs, p->n_sm, s);
-    if (st != BSP_OK) return st;
-    if (ev) BSP_CUDA(cudaEventRecord(ev[2], s));
+    if (ev && part == kPassAll) BSP_CUDA(cudaEventRecord(ev[2], s));
     return BSP_OK;
   }
-  a.st = p->st_full;
-  a.items = p->d_xi;
-  st = launch_xpass<T>(a, p->nxi, p->lines_xy, s);
-  if (st != BSP_OK) return st;
-  if (ev) BSP_CUDA(cudaEventRecord(ev[0], s));
-  a.items = p->d_yi;
-  st = launch_ypass<T>(a, p->nyi, p->lines_xy, s);
-  if (st != BSP_OK) return st;
-  if (ev) BSP_CUDA(cudaEventRecord(ev[1], s));
+  if (part < 0) {
+    a.st = p->st_full;
+    a.items = p->d_xi;
+    st = launch_xpass<T>(a, p->nxi, p->lines_xy, s);
+    if (st != BSP_OK) return st;
+    if (ev) BSP_CUDA(cudaEventRecord(ev[0], s));
+    a.items = p->d_yi;
+    st = launch_ypass<T>(a, p->nyi, p->lines_xy, s);
+    if (st != BSP_OK) return st;
+    if (ev) BSP_CUDA(cudaEventRecord(ev[1], s));
+    if (part == kPassXY) return BSP_OK;
+  }
   a.items = p->d_zi;
+  int nzi = p->nzi;
+  if (part >= 0) {
+    a.items = p->d_zi + p->zi_off[part];
+    nzi = p->zi_off[part + 1] - p->zi_off[part];
+    a.slab_x0 = p->slab_x0(part);
+    a.slab_nx = p->slab_len(part);
+  }
   a.st = p->st_half;
   if (split) a.fields = p->fields32;
-  st = launch_zpass<T>(a, p->nzi, p->lines_z, s);
+  st = launch_zpass<T>(a, nzi, p->lines_z, s);
   if (st != BSP_OK) return st;
   if (split) {
     st = launch_split_fields(static_cast<const float*>(p->fields32), static_cast<uint32_t*>(fields),
                              (long long)p->ns * p->nvox() / 2, p->n_sm, s);
     if (st != BSP_OK) return st;
   }
-  if (ev) BSP_CUDA(cudaEventRecord(ev[2], s));
+  if (ev && part == kPassAll) BSP_CUDA(cudaEventRecord(ev[2], s));
   return BSP_OK;
 }
 
@@ -949,10 +1070,26 @@ bsp_status estimate_impl(bsp_plan* p, const void* spec, double* b_trip, double* 
   cudaEvent_t* ev = rec ? &p->events[(size_t)p->timing_calls * (BSP_N_STAGES + 1)] : nullptr;
   if (rec) BSP_CUDA(cudaEventRecord(ev[0], s));
   const bool split = p->prec == BSP_MIXED_BF16X3;
-  bsp_status st = plan_passes<T>(p, spec, p->fields, s, rec ? ev + 1 : nullptr, split);
-  if (st != BSP_OK) return st;
-  st = run_contract<T>(p, p->fields, p->msum, s, rec ? ev[4] : nullptr, split && p->warp_fft);
-  if (st != BSP_OK) return st;
+  bsp_status st;
+  if (p->slab_nx) {
+    // memory budget: X and Y passes once, then the Z pass and the contraction slab by slab (the
+    // timing's Z-pass stage covers all slabs' Z passes and contractions)
+    st = plan_passes<T>(p, spec, p->fields, s, rec ? ev + 1 : nullptr, false, kPassXY);
+    if (st != BSP_OK) return st;
+    for (int k = 0; k < p->n_slabs(); ++k) {
+      if ((st = plan_passes<T>(p, spec, p->fields, s, nullptr, false, k)) != BSP_OK) return st;
+      if ((st = contract_slab<T>(p, k, s)) != BSP_OK) return st;
+    }
+    if (rec) {
+      BSP_CUDA(cudaEventRecord(ev[3], s));
+      BSP_CUDA(cudaEventRecord(ev[4], s));
+    }
+  } else {
+    st = plan_passes<T>(p, spec, p->fields, s, rec ? ev + 1 : nullptr, split);
+    if (st != BSP_OK) return st;
+    st = run_contract<T>(p, p->fields, p->msum, s, rec ? ev[4] : nullptr, split && p->warp_fft);
+    if (st != BSP_OK) return st;
+  }
   FinalizeArgs f{};
   f.msum = p->msum;
   f.tsum = p->tsum;
@@ -969,8 +1106,16 @@ bsp_status estimate_impl(bsp_plan* p, const void* spec, double* b_trip, double* 
   if (rec) {
     BSP_CUDA(cudaEventRecord(ev[5], s));
     p->timing_calls += 1;
-    const int passes = p->warp_fft ? 3 : (p->nxi > 0) + (p->nyi > 0) + (p->nzi > 0) + (split ? 1 : 0);
-    p->launches += passes + contract_launches(p) + 1;
+    if (p->slab_nx) {
+      int passes = p->warp_fft ? 2 + p->n_slabs() : (p->nxi > 0) + (p->nyi > 0);
+      if (!p->warp_fft)
+        for (int k = 0; k < p->n_slabs(); ++k) passes += p->zi_off[k + 1] > p->zi_off[k];
+      const bool work = !p->levels.empty() && p->levels[0].ntiles > 0;
+      p->launches += passes + 2LL * work * p->n_slabs() + 1;
+    } else {
+      const int passes = p->warp_fft ? 3 : (p->nxi > 0) + (p->nyi > 0) + (p->nzi > 0) + (split ? 1 : 0);
+      p->launches += passes + contract_launches(p) + 1;
+    }
   }
   return BSP_OK;
 }
@@ -1104,7 +1249,7 @@ bsp_status grad_setup(bsp_plan* p, cudaStream_t s) {
   if ((st = dev_upload(p, cnorm, &p->d_cnorm, s)) != BSP_OK) return st;
   if ((st = dev_alloc(p, (size_t)p->adj_entries * sizeof(float), &tmp)) != BSP_OK) return st;
   p->d_w = static_cast<float*>(tmp);
-  if ((st = dev_alloc(p, p->field_bytes(), &tmp)) != BSP_OK) return st;
+  if ((st = dev_alloc(p, p->store_bytes(), &tmp)) != BSP_OK) return st;  // G_n of the grid or of one x-slab
   p->d_gfields = static_cast<float*>(tmp);
   if ((st = dev_alloc(p, (size_t)p->ng * p->ng * (p->ng / 2 + 1) * sizeof(float2), &p->d_grad_spec)) != BSP_OK)
     return st;
@@ -1235,6 +1380,7 @@ bsp_status bsp_plan_create(const bsp_plan_desc* desc, void* stream, bsp_plan** o
   TRY(p->prec == BSP_FP64 ? launch_twiddles<double>(p->tw, p->ngs, s) : launch_twiddles<float>(p->tw, p->ngs, s));
   TRY(dev_upload(p, xi, &p->d_xi, s));
   TRY(dev_upload(p, yi, &p->d_yi, s));
+  slab_items(p->slab_nx, p->ngs, zi, p->zi_off);
   TRY(dev_upload(p, zi, &p->d_zi, s));
   for (const ShellGeom& g : p->geom) p->rmax = std::max(p->rmax, g.r);
   p->warp_fft = p->prec != BSP_FP64 && warp_fft_supported(p->ngs);
@@ -1254,7 +1400,7 @@ bsp_status bsp_plan_create(const bsp_plan_desc* desc, void* stream, bsp_plan** o
   }
   TRY(dev_alloc(p, g1_elems(p) * ce, &p->g1));
   TRY(dev_alloc(p, g2_elems(p) * ce, &p->g2));
-  TRY(dev_alloc(p, p->field_bytes(), &p->fields));
+  TRY(dev_alloc(p, p->store_bytes(), &p->fields));  // all fields, or one x-slab of them
   if (p->prec == BSP_MIXED_BF16X3 && !p->warp_fft) TRY(dev_alloc(p, p->field_bytes(), &p->fields32));
   TRY(build_levels(p, s));
   void* tmp = nullptr;
@@ -1470,6 +1616,13 @@ bsp_status bsp_estimate_host(bsp_plan* p, const void* spec_host, double* b_tripl
   return BSP_OK;
 }
 
+bsp_status bsp_plan_slabs(const bsp_plan* p, int* slab_planes, int* n_slabs) {
+  if (!p || !slab_planes || !n_slabs) return fail(BSP_ERR_INVALID_ARG, "NULL argument");
+  *slab_planes = p->slab_nx;
+  *n_slabs = p->n_slabs();
+  return BSP_OK;
+}
+
 bsp_status bsp_plan_host_input_bytes(const bsp_plan* p, size_t* bytes) {
   if (!p || !bytes) return fail(BSP_ERR_INVALID_ARG, "NULL argument");
   const size_t R = (size_t)p->rmax;
@@ -1557,16 +1710,12 @@ bsp_status bsp_grad(bsp_plan* p, const void* spec, const double* dl_db, float* d
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   bsp_status st = grad_setup(p, s);
   if (st != BSP_OK) return st;
-  // shell fields on the evaluation grid (recomputed: nothing is kept from a forward call)
-  st = plan_passes<float>(p, spec, p->fields, s, nullptr);
-  if (st != BSP_OK) return st;
-  // W and the adjoint products G_n
+  // W, then the shell fields on the evaluation grid (recomputed: nothing is kept from a forward
+  // call), the adjoint products G_n and their forward transforms along z, all at once or, under a
+  // memory budget, one x-slab at a time after a single X and Y pass
   st = launch_build_w(dl_db, p->d_cnorm, p->d_w_ptr, p->d_w_idx, p->adj_entries, p->d_w, s);
   if (st != BSP_OK) return st;
-  st = launch_adjoint_products(static_cast<const float*>(p->fields), p->nvox(), p->ns, p->adj_np, p->d_adj_pairs,
-                               p->adj_npairs, p->d_w, p->d_gfields, p->n_sm, s);
-  if (st != BSP_OK) return st;
-  // forward transforms of G_n, kept on each shell's modes: conj(.) K (ng/S)^3 into the ng spectrum
+  if (p->slab_nx && (st = plan_passes<float>(p, spec, p->fields, s, nullptr, false, kPassXY)) != BSP_OK) return st;
   PassArgs a{};
   a.n_sm = p->n_sm;
   a.g1 = p->g1;
@@ -1581,8 +1730,20 @@ bsp_status bsp_grad(bsp_plan* p, const void* spec, const double* dl_db, float* d
   a.rmax = p->rmax;
   a.stw = p->d_stw;
   a.stw_half = p->d_stw_half;
-  st = launch_warp_zfpass(a, p->d_gfields, (long long)p->ns * p->ngs * p->ngs, p->n_sm, s);
-  if (st != BSP_OK) return st;
+  for (int k = 0; k < p->n_slabs(); ++k) {
+    const int part = p->slab_nx ? k : kPassAll;
+    if ((st = plan_passes<float>(p, spec, p->fields, s, nullptr, false, part)) != BSP_OK) return st;
+    const long long nvox = (long long)p->slab_len(k) * p->ngs * p->ngs;
+    st = launch_adjoint_products(static_cast<const float*>(p->fields), nvox, p->ns, p->adj_np, p->d_adj_pairs,
+                                 p->adj_npairs, p->d_w, p->d_gfields, p->n_sm, s);
+    if (st != BSP_OK) return st;
+    // forward transforms of G_n, kept on each shell's modes: conj(.) K (ng/S)^3 into the ng spectrum
+    a.slab_x0 = p->slab_nx ? p->slab_x0(k) : 0;
+    a.slab_nx = p->slab_nx ? p->slab_len(k) : 0;
+    st = launch_warp_zfpass(a, p->d_gfields, (long long)p->ns * p->slab_len(k) * p->ngs, p->n_sm, s);
+    if (st != BSP_OK) return st;
+  }
+  a.slab_x0 = a.slab_nx = 0;
   a.items = p->d_wyi;
   st = launch_warp_yfpass(a, p->nwyi, s);
   if (st != BSP_OK) return st;

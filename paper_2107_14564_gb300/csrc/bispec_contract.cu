@@ -89,7 +89,8 @@ contract_simt_kernel(ContractArgs a, long long vox_per_block) {
   }
 }
 
-// msum[map[tile][k]] = scale * sum over blocks of partial[block][tile][k], blocks in order.
+// msum[map[tile][k]] = scale * sum over blocks of partial[block][tile][k], blocks in order
+// (added to msum when accumulating x-slabs).
 __global__ void reduce_partials_kernel(ContractArgs a) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= a.ntiles * 16) return;
@@ -97,7 +98,7 @@ __global__ void reduce_partials_kernel(ContractArgs a) {
   if (dst < 0) return;
   double s = 0.0;
   for (int b = 0; b < a.gridx; ++b) s += a.partial[(long long)b * a.ntiles * 16 + idx];
-  a.msum[dst] = a.scale * s;
+  a.msum[dst] = a.accumulate ? a.msum[dst] + a.scale * s : a.scale * s;
 }
 
 template <typename T>

@@ -215,8 +215,10 @@ __global__ void __launch_bounds__(kFftThreads) zpass_kernel(PassArgs a, int max_
   }
   __syncthreads();
   fft_lines<T>(buf, nl, M, a.st, tws, 2);
-  C* out = reinterpret_cast<C*>(static_cast<T*>(a.fields) + (long long)it.n * ng * ng * ng +
-                                ((long long)x * ng + it.v0) * ng);
+  const int nx = a.slab_nx ? a.slab_nx : ng;  // x-planes of each shell in the output
+  const int x0 = a.slab_nx ? a.slab_x0 : 0;
+  C* out = reinterpret_cast<C*>(static_cast<T*>(a.fields) + (long long)it.n * nx * ng * ng +
+                                ((long long)(x - x0) * ng + it.v0) * ng);
   for (int idx = threadIdx.x; idx < nl * M; idx += blockDim.x) out[idx] = buf[idx];
 }
 

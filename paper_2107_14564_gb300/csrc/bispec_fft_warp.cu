@@ -290,7 +290,8 @@ __global__ void __launch_bounds__(XY<N>::kThreads, XPASS ? 4 : 3) xy_warp_kernel
 }
 
 // ---------------------------------------------------------------- Z pass
-template <int S>
+// SLAB: only the x-slab of a.slab_x0 / a.slab_nx, FP32 fields [n][x - slab_x0][y][z].
+template <int S, bool SLAB>
 __global__ void __launch_bounds__(kZThreads, 4) z_warp_kernel(PassArgs a, long long n_lines) {
   constexpr int M = S / 2;
   constexpr int LPL = Radices<M>::lpl;
@@ -322,8 +323,10 @@ __global__ void __launch_bounds__(kZThreads, 4) z_warp_kernel(PassArgs a, long l
   constexpr int BPLL = M / (RL * LPL);
   for (long long line = ((long long)blockIdx.x * (kZThreads / 32) + warp) * LPW + sub; line < n_lines;
        line += stride) {
-    const int n = (int)(line / plane);
-    const long long xy = line - (long long)n * plane;
+    const long long per = SLAB ? (long long)a.slab_nx * S : plane;  // lines of one shell
+    const int n = (int)(line / per);
+    const long long xyl = line - (long long)n * per;                  // line within the shell's output
+    const long long xy = SLAB ? (long long)a.slab_x0 * S + xyl : xyl;  // (x, y) on the grid
     const ShellGeom g = a.geom[n];
     const int r = g.r;
     const float2* src = static_cast<const float2*>(a.g2) + g.g2_off + xy * r;
@@ -340,8 +343,8 @@ __global__ void __launch_bounds__(kZThreads, 4) z_warp_kernel(PassArgs a, long l
         v[b * R1 + rr] = make_float2(e.x - o.y, e.y + o.x);                    // e + i o
       }
     warp_fft_from<M, LPL, 0, 1, false>(v, buf, lane, tw);
-    const long long off = (long long)n * S * plane + xy * S;  // first voxel of the line
-    if (a.split_lo == 0) {
+    const long long off = (long long)n * S * per + xyl * S;  // first voxel of the line
+    if (SLAB || a.split_lo == 0) {
       float2* dst = reinterpret_cast<float2*>(static_cast<float*>(a.fields) + off);
 #pragma unroll
       for (int b = 0; b < BPLL; ++b)
@@ -431,6 +434,7 @@ __global__ void __launch_bounds__(kZThreads, 4) z_warp_kernel(PassArgs a, long l
 //   YF: lines (n, x, k_z) along y, keep |k_y| < r              -> H2[x][k_y][k_z] (G1 layout)
 //   XF: lines (n, k_y, k_z) along x, keep the shell's modes    -> conj(.) K(k) scale into the
 //       half spectrum of the ng grid (Eq. (3.4) factor K when the plan has RSD).
+// With a.slab_nx > 0 the ZF pass takes the lines of one x-slab, G_n laid out [n][x - slab_x0][y][z].
 template <int S>
 __global__ void __launch_bounds__(kZThreads) zf_warp_kernel(PassArgs a, const float* gfield, long long n_lines) {
   constexpr int LPL = Radices<S>::lpl;
@@ -455,11 +459,13 @@ __global__ void __launch_bounds__(kZThreads) zf_warp_kernel(PassArgs a, const fl
   constexpr int BPLL = S / (RL * LPL);
   for (long long line = ((long long)blockIdx.x * (kZThreads / 32) + warp) * LPW + sub; line < n_lines;
        line += stride) {
-    const int n = (int)(line / plane);
-    const long long xy = line - (long long)n * plane;
+    const long long per = a.slab_nx ? (long long)a.slab_nx * S : plane;  // lines of one shell
+    const int n = (int)(line / per);
+    const long long xyl = line - (long long)n * per;
+    const long long xy = (long long)a.slab_x0 * S + xyl;  // slab_x0 is 0 without slabs
     const ShellGeom g = a.geom[n];
     const int r = g.r;
-    const float* src = gfield + (long long)n * S * plane + xy * S;
+    const float* src = gfield + (long long)n * S * per + xyl * S;
     float2 v[E];
 #pragma unroll
     for (int b = 0; b < BPL; ++b)
@@ -615,14 +621,16 @@ bsp_status launch_z(const PassArgs& a, long long n_lines, int n_sm, cudaStream_t
   constexpr int LPW = 32 / Radices<M>::lpl;
   const size_t smem = ((size_t)2 * M + (size_t)(kZThreads / 32) * LPW * pad_len<M>()) * sizeof(float2) +
                       (a.n_zlev > 0 ? (size_t)S * sizeof(uint32_t) : 0);
-  BSP_CUDA(cudaFuncSetAttribute(z_warp_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (a.slab_nx > 0 && a.split_lo != 0) return fail_c(BSP_ERR_NOT_SUPPORTED, "x-slabs of split fields");
+  auto kern = a.slab_nx > 0 ? z_warp_kernel<S, true> : z_warp_kernel<S, false>;
+  BSP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
-  BSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, z_warp_kernel<S>, kZThreads, smem));
+  BSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kZThreads, smem));
   long long blocks = (long long)std::max(per_sm, 1) * n_sm;
   const long long need = (n_lines + (kZThreads / 32) * LPW - 1) / ((kZThreads / 32) * LPW);
   if (blocks > need) blocks = need;
   if (blocks < 1) blocks = 1;
-  z_warp_kernel<S><<<(unsigned)blocks, kZThreads, smem, s>>>(a, n_lines);
+  kern<<<(unsigned)blocks, kZThreads, smem, s>>>(a, n_lines);
   BSP_CUDA(cudaGetLastError());
   return BSP_OK;
 }

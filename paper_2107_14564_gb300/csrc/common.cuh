@@ -74,6 +74,8 @@ struct PassArgs {
   int rsd;
   double beta;
   int kweight;            // generic X pass, counting input only: mode value |k| / k_f instead of 1
+  int slab_x0, slab_nx;   // Z passes: only x in [slab_x0, slab_x0 + slab_nx) of the evaluation grid,
+                          // fields laid out [n][x - slab_x0][y][z]; slab_nx = 0: the whole grid
   FftStages st;           // stage list of this pass's line length
   int rmax;               // largest r of all shells
   int n_sm;               // SMs of the device (grid size of the persistent warp kernels)
@@ -152,6 +154,7 @@ struct ContractArgs {
   double* msum;           // [n_out]
   int n_out;
   double scale;           // msum = scale * (sum over the evaluation grid)
+  int accumulate;         // reduce: msum += instead of msum = (later x-slabs of one sum)
 };
 template <typename T>
 bsp_status launch_contract_simt(const ContractArgs& a, cudaStream_t s);

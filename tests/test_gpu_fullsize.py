@@ -22,15 +22,23 @@ def lib():
     return binding
 
 
-def _sampled(lib, ng, ns, top, n_index, f, seed, beta, prec, picks):
+def _sampled(lib, ng, ns, top, n_index, f, seed, beta, prec, picks, budgets=(0,)):
+    """Condition-scaled and plain relative errors of the picked bins, one row per memory budget."""
     edges = np.linspace(1.0, top, ns + 1)
     delta = fieldgen.quadratic_field(ng, float(ng), n_index, f, seed)
     spec = fieldgen.half_spectrum_c64(delta)
     del delta
-    gp = lib.Plan(ng, float(ng), edges, 20, 20, rsd=beta is not None, beta=beta or 0.0, precision=prec)
-    b = gp.estimate(torch.from_numpy(spec).cuda(), with_grid=False)[0].cpu().numpy()
-    gp.check()
-    tr = gp.triplets
+    bs = []
+    for budget in budgets:
+        gp = lib.Plan(ng, float(ng), edges, 20, 20, rsd=beta is not None, beta=beta or 0.0, precision=prec,
+                      mem_budget_bytes=budget)
+        if budget:  # fields produced and reduced x-slab by x-slab; the plan holds less than all fields
+            assert gp.slabs[1] > 1 and gp.device_bytes < gp.field_bytes
+        bs.append(gp.estimate(torch.from_numpy(spec).cuda(), with_grid=False)[0].cpu().numpy())
+        gp.check()
+        tr = gp.triplets
+        gp.close()
+        torch.cuda.empty_cache()
     keys = [(int(a), int(bb), int(c)) for a, bb, c in zip(tr["a"], tr["b"], tr["c"])]
     pl = P.make_plan(ng, float(ng), edges, 20, 20)
     assert len(keys) <= len(pl.candidates)
@@ -49,7 +57,7 @@ def _sampled(lib, ng, ns, top, n_index, f, seed, beta, prec, picks):
     norm = pl.vcell ** 3 / pl.volume
     want = norm * msum / tsum
     scale = norm * asum / tsum
-    got = b[picks]
+    got = np.stack([b[picks] for b in bs])
     assert np.array_equal(np.rint(tsum / float(ng) ** 3), tr["ntri"][picks])
     cond = np.abs(got - want) / scale
     rel = np.abs(got - want) / np.abs(want)
@@ -70,9 +78,10 @@ def test_ng256_fp32_sampled_bins(lib):
 
 
 def test_ng768_fp32_forward_sampled_bins(lib):
-    """The forward-only Ng=768 FP32 workload (24 shells k_f..192 k_f): every field stays
-    resident (24 x 768^3 FP32 = 43.5 GB); bins of the largest, a middle and the smallest k1
-    shell against the oracle."""
+    """The forward-only Ng=768 FP32 workload (24 shells k_f..192 k_f), with every field resident
+    (24 x 768^3 FP32 = 43.5 GB) and under an 8 GiB budget for shell fields (x-slabs of 151
+    planes, plan-time FP64 counts in slabs too); bins of the largest, a middle and the smallest
+    k1 shell against the oracle."""
     picks = [-1, -2, 300, 0]
-    cond, rel = _sampled(lib, 768, 24, 192.0, 1.5, 0.05, 7, None, "fp32", picks)
+    cond, rel = _sampled(lib, 768, 24, 192.0, 1.5, 0.05, 7, None, "fp32", picks, budgets=(0, 8 << 30))
     assert np.max(cond) < 1e-4, (cond, rel)

@@ -117,3 +117,26 @@ def test_adjoint_on_a_384_evaluation_grid(lib):
     gp.check()
     err = np.abs(got - want).max() / np.abs(want).max()
     assert err < 1e-4, err
+
+
+def test_adjoint_under_a_memory_budget(lib):
+    """Shell fields, adjoint products and their transforms along z one x-slab at a time (slabs of
+    20 planes of the 128^3 evaluation grid, the last one 8), with RSD: the gradient and the
+    estimate against the oracle."""
+    ng, beta = 128, 0.5
+    edges = P.linear_edges(8, 1.0, 32.0)
+    delta = fieldgen.quadratic_field(ng, float(ng), 1.5, 0.2, 5).astype(np.float32)
+    gp = lib.Plan(ng, float(ng), edges, rsd=True, beta=beta, precision="fp32",
+                  mem_budget_bytes=20 * 8 * 128 * 128 * 4)
+    assert gp.ng_eval == 128 and gp.slabs == (20, 7)
+    pl = P.make_plan(ng, float(ng), edges)
+    trips = [tuple(int(v) for v in t) for t in zip(gp.triplets["a"], gp.triplets["b"], gp.triplets["c"])]
+    g = fieldgen.random_weights(len(trips), 9)
+    want = G.vjp(delta.astype(np.float64), pl, trips, gp.triplets["tsum"], g, beta=beta)
+    spec = gp.spectrum(torch.from_numpy(delta).cuda())
+    got = gp.grad(spec, torch.from_numpy(g).cuda()).cpu().numpy()
+    b, _ = gp.estimate(spec)
+    gp.check()
+    assert np.abs(got - want).max() / np.abs(want).max() < 1e-4
+    res = fbe.estimate(spec.cpu().numpy().astype(np.complex128), pl, beta=beta, with_abs=True)
+    assert np.max(np.abs(b.cpu().numpy() - res["b"]) / res["b_scale"]) < 1e-4

@@ -351,3 +351,34 @@ def test_triangle_mean_labels(lib):
     b0, _ = shell.estimate(torch.from_numpy(spec).cuda())
     assert np.array_equal(b.cpu().numpy(), b0.cpu().numpy())
     assert np.max(np.abs(b.cpu().numpy() - res["b"]) / np.abs(res["b"])) < 1e-10
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_memory_budget_slabs(lib, prec):
+    """Under a budget of 7 x-planes of shell fields the plan produces and reduces the fields one
+    x-slab of the evaluation grid at a time (the last slab thinner), and counts the triangles at
+    plan time in slabs too: plan tables exact, values against the oracle and against the plan
+    that holds every field."""
+    ng = 64
+    edges = _edges(ng, 12)
+    spec = _spec(ng, 1.5, 0.05, 27, c64=prec != "fp64")
+    pl, res = _oracle(spec, ng, edges, with_abs=True)
+    full = lib.Plan(ng, float(ng), edges, precision=prec)
+    size = full.ng_eval
+    elem = 8 if prec == "fp64" else 4
+    gp = lib.Plan(ng, float(ng), edges, precision=prec, mem_budget_bytes=7 * 12 * size * size * elem)
+    assert gp.slabs == (7, -(-size // 7)) and size % 7 != 0
+    assert full.slabs == (0, 1)
+    assert gp.device_bytes < full.device_bytes
+    _check_plan_tables(gp, res, pl)
+    b, g = gp.estimate(torch.from_numpy(spec).cuda())
+    b0, _ = full.estimate(torch.from_numpy(spec).cuda())
+    gp.check()
+    b, b0, g = b.cpu().numpy(), b0.cpu().numpy(), g.cpu().numpy()
+    if prec == "fp64":
+        assert np.max(np.abs(b - res["b"]) / np.abs(res["b"])) < 1e-10
+        assert np.max(np.abs(b - b0) / res["b_scale"]) < 1e-13
+    else:
+        assert np.max(_cond_err(b, res)) < 1e-4
+        assert np.max(np.abs(b - b0) / res["b_scale"]) < 1e-5
+    assert np.array_equal(np.isnan(g), np.isnan(res["grid"]))
