@@ -20,8 +20,8 @@ from __future__ import annotations
 import numpy as np
 import scipy.fft as sfft
 
-__all__ = ["gaussian_field", "quadratic_field", "spectrum", "half_spectrum_c64",
-           "random_voxels", "random_weights"]
+__all__ = ["gaussian_field", "quadratic_field", "gaussian_field_2d", "quadratic_field_2d", "spectrum",
+           "half_spectrum_c64", "random_voxels", "random_weights"]
 
 
 def _kmag_half(ng: int, box_len: float) -> np.ndarray:
@@ -53,6 +53,27 @@ def quadratic_field(ng: int, box_len: float, n_index: float, f_ng: float, seed: 
                     workers: int = -1) -> np.ndarray:
     """Local quadratic non-Gaussian field of Eq. (3.1) built on gaussian_field (float64)."""
     dg = gaussian_field(ng, box_len, n_index, seed, workers)
+    sq = dg * dg
+    return dg + f_ng * (sq - sq.mean())
+
+
+def gaussian_field_2d(ng: int, box_len: float, n_index: float, seed: int) -> np.ndarray:
+    """The 2D counterpart of gaussian_field on an Ng^2 grid of a square of side L (the 2D box of
+    Sec. 2.1): < |A_c DFT[delta_G](k)|^2 > = A P(k), A = L^2, A_c = (L / Ng)^2 (float64)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    wk = sfft.rfftn(rng.standard_normal((ng, ng)))
+    m = np.fft.fftfreq(ng, d=1.0 / ng)
+    my = np.arange(ng // 2 + 1, dtype=np.float64)
+    k = (2.0 * np.pi / box_len) * np.sqrt(m[:, None] ** 2 + my[None, :] ** 2)
+    k[0, 0] = 1.0
+    amp = np.sqrt(k ** (-n_index) / (box_len / ng) ** 2)
+    amp[0, 0] = 0.0
+    return sfft.irfftn(wk * amp, s=(ng, ng))
+
+
+def quadratic_field_2d(ng: int, box_len: float, n_index: float, f_ng: float, seed: int) -> np.ndarray:
+    """Eq. (3.1) on gaussian_field_2d (float64, [x][y], y the axis the real FFT halves)."""
+    dg = gaussian_field_2d(ng, box_len, n_index, seed)
     sq = dg * dg
     return dg + f_ng * (sq - sq.mean())
 
