@@ -98,6 +98,12 @@ typedef struct {
   int k1_merge;            /* (mu, t) cells span this many neighbouring k1 shells (Sec. 2.1, last
                               paragraph: merging adjacent bins); 0 or 1: one shell per cell group */
   int label_k;             /* a bsp_label_k: the lengths the labels (mu, t) are formed from */
+  int dim;                 /* 0 or 3: an Ng^3 cube binned in spherical shells. 2: an Ng^2 square of
+                              side L binned in annular rings (the 2D box of Sec. 2.1): ng even up
+                              to 4096, spectrum [Ng][Ng/2 + 1] (the last axis halved), fields
+                              [N_s][S][S], B = A_c^3 sum d d d / (A sum i i i) with the cell area
+                              A_c = (L / Ng)^2 and A = L^2; BSP_FP64 or BSP_FP32 only, without RSD,
+                              triangle-mean labels, memory budget, bsp_spectrum or bsp_grad. */
 } bsp_plan_desc;
 
 /* One bin of triangles (Sec. 2.1): shells a >= b >= c and their labels (Eq. (2.4)). */

@@ -24,7 +24,8 @@ class PlanDesc(C.Structure):
                 ("rsd", C.c_int), ("beta", C.c_double), ("precision", C.c_int),
                 ("mem_budget_bytes", C.c_size_t), ("autotune", C.c_int),
                 ("k1_merge", C.c_int),
-                ("label_k", C.c_int)]
+                ("label_k", C.c_int),
+                ("dim", C.c_int)]
 
 
 class Triplet(C.Structure):

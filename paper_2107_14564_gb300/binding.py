@@ -195,11 +195,12 @@ class Plan:
     this many neighbouring k1 shells (b_grid has ceil(Ns / k1_merge) groups); label_k: 'shell'
     forms (mu, t) from the shells' mean |k|, 'triangle' from the mean sides of each bin's
     triangles; mem_budget_bytes: the most bytes of shell fields to hold at once (0: all; else
-    fields are produced and reduced x-slab by x-slab, see .slabs)."""
+    fields are produced and reduced x-slab by x-slab, see .slabs); dim: 3 for an Ng^3 cube in
+    spherical shells, 2 for an Ng^2 square in annular rings (spectrum [Ng, Ng/2+1])."""
 
     def __init__(self, ng, box_len, edges_kf, n_mu=10, n_t=10, rsd=False, beta=0.0,
                  precision="fp32", stream=None, autotune=False, k1_merge=1,
-                 label_k="shell", mem_budget_bytes=0):
+                 label_k="shell", mem_budget_bytes=0, dim=3):
         self._edges = np.ascontiguousarray(np.asarray(edges_kf, dtype=np.float64))
         desc = PlanDesc()
         desc.ng = int(ng)
@@ -217,9 +218,11 @@ class Plan:
         if label_k not in ("shell", "triangle"):
             raise ValueError("label_k must be 'shell' or 'triangle'")
         desc.label_k = 0 if label_k == "shell" else 1
+        desc.dim = int(dim)
         self.handle = None
         self.handle = bsp_plan_create(desc, stream)
         self.ng, self.box_len, self.n_mu, self.n_t = int(ng), float(box_len), int(n_mu), int(n_t)
+        self.dim = 2 if dim == 2 else 3
         self.precision = precision
         self.real_dtype = torch.float64 if precision == "fp64" else torch.float32
         self.complex_dtype = torch.complex128 if precision == "fp64" else torch.complex64
@@ -244,7 +247,7 @@ class Plan:
             pass
 
     def spec_shape(self):
-        return (self.ng, self.ng, self.ng // 2 + 1)
+        return (self.ng,) * (self.dim - 1) + (self.ng // 2 + 1,)
 
     def _check_spec(self, spec: torch.Tensor):
         if not spec.is_cuda or spec.dtype != self.complex_dtype or tuple(spec.shape) != self.spec_shape() \
@@ -295,13 +298,13 @@ class Plan:
     def shell_fields(self, spec: torch.Tensor, stream=None) -> torch.Tensor:
         self._check_spec(spec)
         s = self.ng_eval
-        out = torch.empty((self.n_shells, s, s, s), dtype=self.real_dtype, device=spec.device)
+        out = torch.empty((self.n_shells,) + (s,) * self.dim, dtype=self.real_dtype, device=spec.device)
         bsp_shell_fields(self.handle, spec, out, stream)
         return out
 
     def contract(self, fields: torch.Tensor, stream=None) -> torch.Tensor:
         if not fields.is_cuda or fields.dtype != self.real_dtype or not fields.is_contiguous() \
-                or fields.numel() != self.n_shells * self.ng_eval ** 3:
+                or fields.numel() != self.n_shells * self.ng_eval ** self.dim:
             raise ValueError("fields must be the contiguous [Ns, S, S, S] output of shell_fields")
         msum = torch.empty(self.n_triplets, dtype=torch.float64, device=fields.device)
         bsp_contract(self.handle, fields, msum, stream)

@@ -100,7 +100,8 @@ struct ContractLevel {
   int gridy_cap = 0;          // voxel blocks the partial-sum buffer holds
   int tune_mult = 1;          // blocks per M tile / SM count chosen by the autotuner (1 without it)
   double* tc_partial = nullptr;
-  long long nvox() const { return (long long)g * g * g; }
+  int dim = 3;                // 2: a level of a 2D plan (g^2 points)
+  long long nvox() const { return dim == 2 ? (long long)g * g : (long long)g * g * g; }
 };
 
 constexpr int kNumTune = 3;
@@ -112,6 +113,7 @@ struct bsp_plan {
   int autotune = 0;
   int k1_merge = 1;         // k1 shells per (mu, t) cell group
   int label_k = BSP_LABEL_SHELL_MEAN;
+  int dim = 3;              // 2: Ng^2 square with annular rings (Sec. 2.1); 3: Ng^3 cube with shells
   size_t mem_budget = 0;    // bytes of shell fields the plan may hold at once (0: no limit)
   int slab_nx = 0;          // > 0: estimates stream x-slabs of this many planes of the evaluation grid
   std::vector<int> zi_off;  // generic Z items of slab k: [zi_off[k], zi_off[k + 1])
@@ -182,10 +184,10 @@ struct bsp_plan {
   double* bgrid_dev = nullptr;
 
   size_t elem() const { return prec == BSP_FP64 ? sizeof(double) : sizeof(float); }
-  long long nvox() const { return (long long)ngs * ngs * ngs; }  // voxels of the evaluation grid
+  long long nvox() const { return dim == 2 ? (long long)ngs * ngs : (long long)ngs * ngs * ngs; }  // evaluation grid
   int n_groups() const { return (ns + k1_merge - 1) / k1_merge; }
   int n_cells() const { return n_groups() * n_mu * n_t; }
-  size_t spec_bytes() const { return (size_t)ng * ng * (ng / 2 + 1) * 2 * elem(); }
+  size_t spec_bytes() const { return (size_t)(dim == 2 ? 1 : ng) * ng * (ng / 2 + 1) * 2 * elem(); }
   size_t field_bytes() const { return (size_t)ns * (size_t)nvox() * elem(); }
   int n_slabs() const { return slab_nx ? (ngs + slab_nx - 1) / slab_nx : 1; }
   int slab_x0(int k) const { return k * slab_nx; }
@@ -267,6 +269,15 @@ void make_items_g(const std::vector<ShellGeom>& geom, int grid, int lines_xy, in
 
 void make_items(const bsp_plan* p, int lines_xy, int lines_z, std::vector<Item>& xi,
                 std::vector<Item>& yi, std::vector<Item>& zi) {
+  if (p->dim == 2) {  // 2D rings: k_y lines for the X pass (xi), x rows for the C2R along y (zi)
+    xi.clear(); yi.clear(); zi.clear();
+    for (int n = 0; n < p->ns; ++n) {
+      const int r = p->geom[n].r;
+      for (int ky0 = 0; ky0 < r; ky0 += lines_xy) xi.push_back({n, 0, ky0, std::min(lines_xy, r - ky0)});
+      for (int x0 = 0; x0 < p->ngs; x0 += lines_z) zi.push_back({n, 0, x0, std::min(lines_z, p->ngs - x0)});
+    }
+    return;
+  }
   make_items_g(p->geom, p->ngs, lines_xy, lines_z, xi, yi, zi);
 }
 
@@ -362,6 +373,17 @@ bsp_status run_passes(const bsp_plan* p, const void* spec, int rsd, void* tw, vo
   a.rsd = rsd;
   a.beta = p->beta;
   bsp_status st;
+  if (p->dim == 2) {  // 2D rings: X pass, then the C2R along y (the Z-pass kernel on its rows)
+    a.st = p->st_full;
+    a.items = xi;
+    if ((st = launch_ring_xpass<T>(a, nxi, lines_xy, s)) != BSP_OK) return st;
+    a.items = zi;
+    a.st = p->st_half;
+    a.g2 = g1;
+    a.slab_x0 = 0;
+    a.slab_nx = 1;
+    return launch_zpass<T>(a, nzi, lines_z, s);
+  }
   if (do_xy) {
     a.st = p->st_full;
     a.items = xi;
@@ -392,8 +414,15 @@ int pick_gridx(const bsp_plan* p, int ntiles) { return pick_gridx_n(p->n_sm, nti
 
 bsp_status validate(const bsp_plan_desc* d) {
   if (!d) return fail(BSP_ERR_INVALID_ARG, "desc is NULL");
-  if (d->ng < 16 || d->ng > 1024 || (d->ng % 2) != 0)
+  if (d->dim != 0 && d->dim != 2 && d->dim != 3) return fail(BSP_ERR_INVALID_ARG, "dim must be 0, 2 or 3");
+  if (d->dim == 2) {
+    if (d->ng < 16 || d->ng > 4096 || (d->ng % 2) != 0)
+      return fail(BSP_ERR_NOT_SUPPORTED, "2D: ng must be even and within [16, 4096]");
+    if (d->precision == BSP_MIXED_BF16X3 || d->rsd || d->label_k != BSP_LABEL_SHELL_MEAN || d->mem_budget_bytes)
+      return fail(BSP_ERR_NOT_SUPPORTED, "2D plans: FP64 or FP32, no RSD, shell-mean labels, no memory budget");
+  } else if (d->ng < 16 || d->ng > 1024 || (d->ng % 2) != 0) {
     return fail(BSP_ERR_NOT_SUPPORTED, "ng must be even and within [16, 1024]");
+  }
   FftStages st;
   if (!make_stages(d->ng, &st) || !make_stages(d->ng / 2, &st))
     return fail(BSP_ERR_NOT_SUPPORTED, "ng must be a product of 2s and 3s");
@@ -440,13 +469,13 @@ void choose_eval_grid(bsp_plan* p) {
   for (int sz = 16; sz < p->ng; ++sz) {
     if (sz < need || !fft_size_ok(sz)) continue;
     // FP32 plans prefer the sizes the warp-per-line kernels handle
-    if (p->prec != BSP_FP64 && p->ng >= 128 && !warp_fft_supported(sz)) continue;
+    if (p->dim == 3 && p->prec != BSP_FP64 && p->ng >= 128 && !warp_fft_supported(sz)) continue;
     best = sz;
     break;
   }
   p->ngs = best;
   const double f = (double)p->ng / (double)p->ngs;
-  p->sum_scale = f * f * f;
+  p->sum_scale = p->dim == 2 ? f * f : f * f * f;
 }
 
 // Host part of the plan (Sec. 2.1): thresholds, cap, mode counts, means, geometry.
@@ -461,6 +490,7 @@ bsp_status host_plan(bsp_plan* p, const bsp_plan_desc* d) {
   p->autotune = d->autotune;
   p->k1_merge = d->k1_merge > 1 ? d->k1_merge : 1;
   p->label_k = d->label_k;
+  p->dim = d->dim == 2 ? 2 : 3;
   p->box_len = d->box_len;
   p->edges.assign(d->edges_kf, d->edges_kf + d->n_shells + 1);
   p->q.resize(p->ns + 1);
@@ -482,6 +512,10 @@ bsp_status host_plan(bsp_plan* p, const bsp_plan_desc* d) {
     for (long long y = -rr; y <= rr; ++y) {
       const long long qxy = x * x + y * y;
       if (qxy >= qmax) continue;
+      if (p->dim == 2) {  // rings: modes of the plane
+        cnt[qxy] += 1;
+        continue;
+      }
       for (long long z = -rr; z <= rr; ++z) {
         const long long qq = qxy + z * z;
         if (qq < qmax) cnt[qq] += 1;
@@ -516,6 +550,11 @@ bsp_status host_plan(bsp_plan* p, const bsp_plan_desc* d) {
     g.pad = 0;
     g.g1_off = o1;
     g.g2_off = o2;
+    if (p->dim == 2) {  // one buffer of X-pass rows [x][k_y < r], read again by the C2R along y
+      g.g2_off = o1;
+      o1 += (long long)p->ngs * g.r;
+      continue;
+    }
     o1 += (long long)p->ngs * (2 * g.r - 1) * g.r;
     o2 += (long long)p->ngs * p->ngs * g.r;
   }
@@ -547,10 +586,12 @@ void slab_items(int slab_nx, int grid, std::vector<Item>& zi, std::vector<int>& 
 
 long long g1_elems(const bsp_plan* p) {
   const ShellGeom& g = p->geom.back();
+  if (p->dim == 2) return g.g1_off + (long long)p->ngs * g.r;  // 2D X-pass rows [x][k_y < r]
   return g.g1_off + (long long)p->ngs * (2 * g.r - 1) * g.r;
 }
 long long g2_elems(const bsp_plan* p) {
   const ShellGeom& g = p->geom.back();
+  if (p->dim == 2) return 1;  // unused by 2D plans
   return g.g2_off + (long long)p->ngs * p->ngs * g.r;
 }
 
@@ -631,7 +672,7 @@ bsp_status build_levels(bsp_plan* p, cudaStream_t s) {
     }
     const int need = p->geom[p->trips[t].a].r + p->geom[p->trips[t].b].r + p->geom[cmax].r - 2;
     int g = S;
-    for (int cand = 16; cand < S && !p->slab_nx; cand += 8)  // x-slab plans: one level
+    for (int cand = 16; cand < S && !p->slab_nx && p->dim == 3; cand += 8)  // x-slab and 2D plans: one level
       if (S % cand == 0 && cand >= need) { g = cand; break; }
     std::vector<int>& v = bins_of(g);
     for (size_t w = t; w < u; ++w) v.push_back((int)w);
@@ -644,10 +685,11 @@ bsp_status build_levels(bsp_plan* p, cudaStream_t s) {
   std::vector<int> zt;     // their strides
   for (auto& e : by_g) {
     ContractLevel L;
+    L.dim = p->dim;
     L.g = e.first;
     L.stride = S / L.g;
     const double f = (double)p->ng / (double)L.g;
-    L.scale = f * f * f;
+    L.scale = p->dim == 2 ? f * f : f * f * f;
     L.top = L.g == S;
     L.bins = e.second;
     std::vector<int> loc(p->ns, -1);
@@ -789,7 +831,7 @@ bsp_status plan_sums(bsp_plan* p, bool lengths, const std::vector<int>& ca, cons
   std::vector<int> zoff;
   slab_items(slab, S, zi, zoff);
   const int nsl = (int)zoff.size() - 1;
-  const long long slab_vox = (long long)nx * S * S;
+  const long long slab_vox = p->dim == 2 ? (long long)S * S : (long long)nx * S * S;
   std::vector<void*> tmp;
   auto cleanup = [&]() {
     cudaStreamSynchronize(s);
@@ -1031,6 +1073,23 @@ bsp_status plan_passes(bsp_plan* p, const void* spec, void* fields, cudaStream_t
     if (ev && part == kPassAll) BSP_CUDA(cudaEventRecord(ev[2], s));
     return BSP_OK;
   }
+  if (p->dim == 2) {  // 2D rings: X pass, then the C2R along y on its rows (the Y stage is empty)
+    a.st = p->st_full;
+    a.items = p->d_xi;
+    if ((st = launch_ring_xpass<T>(a, p->nxi, p->lines_xy, s)) != BSP_OK) return st;
+    if (ev) {
+      BSP_CUDA(cudaEventRecord(ev[0], s));
+      BSP_CUDA(cudaEventRecord(ev[1], s));
+    }
+    a.items = p->d_zi;
+    a.st = p->st_half;
+    a.g2 = p->g1;
+    a.slab_x0 = 0;
+    a.slab_nx = 1;
+    if ((st = launch_zpass<T>(a, p->nzi, p->lines_z, s)) != BSP_OK) return st;
+    if (ev) BSP_CUDA(cudaEventRecord(ev[2], s));
+    return BSP_OK;
+  }
   if (part < 0) {
     a.st = p->st_full;
     a.items = p->d_xi;
@@ -1097,8 +1156,8 @@ bsp_status estimate_impl(bsp_plan* p, const void* spec, double* b_trip, double* 
   f.cell_ptr = p->cell_ptr;
   f.cell_idx = p->cell_idx;
   f.n_cells = p->n_cells();
-  const double vc = pow(p->box_len / p->ng, 3.0);
-  f.norm = vc * vc * vc / (p->box_len * p->box_len * p->box_len);
+  const double vc = pow(p->box_len / p->ng, (double)p->dim);  // cell volume (area in 2D)
+  f.norm = vc * vc * vc / pow(p->box_len, (double)p->dim);
   f.b_trip = b_trip;
   f.b_grid = b_grid;
   st = launch_finalize(f, s);
@@ -1126,7 +1185,18 @@ void stage_work(const bsp_plan* p, double* bytes, double* flops) {
   const double re = (double)p->elem();
   const double ng = (double)p->ngs;
   for (int i = 0; i < BSP_N_STAGES; ++i) { bytes[i] = 0.0; flops[i] = 0.0; }
-  for (int n = 0; n < p->ns; ++n) {
+  for (int n = 0; n < p->ns && p->dim == 2; ++n) {  // 2D: X pass over k_y < r lines, C2R along y
+    const ShellGeom& g = p->geom[n];
+    long long modes_half = 0;
+    for (int ky = 0; ky < g.r; ++ky)
+      for (int kx = -(g.r - 1); kx <= g.r - 1; ++kx) {
+        const long long q = (long long)kx * kx + (long long)ky * ky;
+        if (q >= g.qlo && q < g.qhi) modes_half += 1;
+      }
+    bytes[BSP_STAGE_XPASS] += ce * (double)modes_half + ce * ng * g.r;
+    bytes[BSP_STAGE_ZPASS] += ce * ng * g.r + re * ng * ng;
+  }
+  for (int n = 0; n < p->ns && p->dim == 3; ++n) {
     const ShellGeom& g = p->geom[n];
     const int r = g.r;
     long long modes_half = 0, xlines = 0;
@@ -1297,7 +1367,7 @@ bsp_status bsp_plan_create(const bsp_plan_desc* desc, void* stream, bsp_plan** o
   st = plan_sums(p, false, ca, cb, cc, nullptr, tsum, s);
   if (st != BSP_OK) { bsp_plan_destroy(p); return st; }
   for (double& t : tsum) t *= p->sum_scale;  // sums over the ng^3 grid (exact up to rounding)
-  const double ng3 = (double)p->ng * (double)p->ng * (double)p->ng;
+  const double ng3 = p->dim == 2 ? (double)p->ng * (double)p->ng : (double)p->ng * (double)p->ng * (double)p->ng;
   std::vector<int> ka, kb, kc;
   std::vector<double> kt;
   for (size_t i = 0; i < ca.size(); ++i) {
@@ -1383,7 +1453,7 @@ bsp_status bsp_plan_create(const bsp_plan_desc* desc, void* stream, bsp_plan** o
   slab_items(p->slab_nx, p->ngs, zi, p->zi_off);
   TRY(dev_upload(p, zi, &p->d_zi, s));
   for (const ShellGeom& g : p->geom) p->rmax = std::max(p->rmax, g.r);
-  p->warp_fft = p->prec != BSP_FP64 && warp_fft_supported(p->ngs);
+  p->warp_fft = p->dim == 3 && p->prec != BSP_FP64 && warp_fft_supported(p->ngs);
   if (p->warp_fft) {
     std::vector<float2> t1, t2;
     warp_stage_table(p->ngs, t1);
@@ -1587,8 +1657,20 @@ bsp_status bsp_estimate_host(bsp_plan* p, const void* spec_host, double* b_tripl
   }
   // Only the modes the shells can reach are read by the estimator: |m_x|, |m_y| <= R - 1 and
   // 0 <= m_z <= R - 1 with R = r of the outermost shell. Copy that box (four boxes in the
-  // wrapped index ranges); the rest of the device copy is never read.
-  {
+  // wrapped index ranges); the rest of the device copy is never read. 2D: rows |m_x| <= R - 1,
+  // their first R entries (0 <= m_y <= R - 1).
+  if (p->dim == 2) {
+    const int ng = p->ng, hy = ng / 2 + 1, R = p->rmax;
+    const size_t ce = 2 * p->elem();
+    const int lo[2] = {0, ng - (R - 1)}, len[2] = {R, R - 1};
+    for (int bx = 0; bx < 2; ++bx) {
+      if (len[bx] <= 0) continue;
+      const size_t off = (size_t)lo[bx] * hy * ce;
+      BSP_CUDA(cudaMemcpy2DAsync(static_cast<char*>(p->spec_dev) + off, (size_t)hy * ce,
+                                 static_cast<const char*>(spec_host) + off, (size_t)hy * ce, (size_t)R * ce,
+                                 (size_t)len[bx], cudaMemcpyHostToDevice, s));
+    }
+  } else {
     const int ng = p->ng, hz = ng / 2 + 1, R = p->rmax;
     const size_t ce = 2 * p->elem();
     const int lo[2] = {0, ng - (R - 1)}, len[2] = {R, R - 1};
@@ -1626,7 +1708,7 @@ bsp_status bsp_plan_slabs(const bsp_plan* p, int* slab_planes, int* n_slabs) {
 bsp_status bsp_plan_host_input_bytes(const bsp_plan* p, size_t* bytes) {
   if (!p || !bytes) return fail(BSP_ERR_INVALID_ARG, "NULL argument");
   const size_t R = (size_t)p->rmax;
-  *bytes = (2 * R - 1) * (2 * R - 1) * R * 2 * p->elem();
+  *bytes = (p->dim == 2 ? 1 : 2 * R - 1) * (2 * R - 1) * R * 2 * p->elem();
   return BSP_OK;
 }
 
@@ -1674,7 +1756,7 @@ bsp_status bsp_plan_stage_work(const bsp_plan* p, double* bytes, double* flops) 
 
 bsp_status bsp_spectrum(bsp_plan* p, const float* delta_x, void* spec_out, void* stream) {
   if (!p || !delta_x || !spec_out) return fail(BSP_ERR_INVALID_ARG, "NULL argument");
-  if (p->prec == BSP_FP64) return fail(BSP_ERR_NOT_SUPPORTED, "bsp_spectrum needs an FP32 or mixed plan");
+  if (p->prec == BSP_FP64 || p->dim == 2) return fail(BSP_ERR_NOT_SUPPORTED, "bsp_spectrum needs a 3D FP32 or mixed plan");
   if (!warp_fft_supported(p->ng)) return fail(BSP_ERR_NOT_SUPPORTED, "bsp_spectrum needs ng = 2^p or 3 * 2^p in [128, 1024]");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   bsp_status st = ball_setup(p, s);
@@ -1704,7 +1786,7 @@ bsp_status bsp_spectrum(bsp_plan* p, const float* delta_x, void* spec_out, void*
 
 bsp_status bsp_grad(bsp_plan* p, const void* spec, const double* dl_db, float* dl_ddelta, void* stream) {
   if (!p || !spec || !dl_db || !dl_ddelta) return fail(BSP_ERR_INVALID_ARG, "NULL argument");
-  if (p->prec == BSP_FP64) return fail(BSP_ERR_NOT_SUPPORTED, "bsp_grad needs an FP32 or mixed plan");
+  if (p->prec == BSP_FP64 || p->dim == 2) return fail(BSP_ERR_NOT_SUPPORTED, "bsp_grad needs a 3D FP32 or mixed plan");
   if (!warp_fft_supported(p->ngs) || !warp_fft_supported(p->ng))
     return fail(BSP_ERR_NOT_SUPPORTED, "bsp_grad needs grid sides 2^p or 3 * 2^p in [128, 1024]");
   cudaStream_t s = static_cast<cudaStream_t>(stream);

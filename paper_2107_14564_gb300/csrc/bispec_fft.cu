@@ -222,6 +222,49 @@ __global__ void __launch_bounds__(kFftThreads) zpass_kernel(PassArgs a, int max_
   for (int idx = threadIdx.x; idx < nl * M; idx += blockDim.x) out[idx] = buf[idx];
 }
 
+// ---------------------------------------------------------------- 2D rings: X pass
+// Item (n, -, v0, cnt): the k_y lines v0 .. v0 + cnt - 1 of ring n (|k_y| < r, k_y >= 0 on the
+// halved axis). Gathers the ring's modes along k_x (|k_x| < r) from the 2D half spectrum
+// [ng][ng/2 + 1], transforms along x on the evaluation grid (length ngs) and writes
+// G[g1_off + x r + k_y], the rows the C2R along y then reads.
+template <typename T>
+__global__ void __launch_bounds__(kFftThreads) ring_xpass_kernel(PassArgs a, int max_lines) {
+  using C = cplx<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  const int ng = a.ng;
+  const int S = a.ngs;
+  C* tws = buf + (size_t)max_lines * S;
+  const Item it = a.items[blockIdx.x];
+  const ShellGeom g = a.geom[it.n];
+  const int nl = it.cnt;
+  load_twiddles<T>(tws, a.tw, S);
+  for (int i = threadIdx.x; i < nl * S; i += blockDim.x) buf[i] = c_make<C>(T(0), T(0));
+  __syncthreads();
+  const int r = g.r;
+  const int w = 2 * r - 1;
+  const int hy = ng / 2 + 1;
+  const C* spec = static_cast<const C*>(a.spec);
+  for (int idx = threadIdx.x; idx < w * nl; idx += blockDim.x) {
+    const int l = idx % nl;
+    const int mx = idx / nl - (r - 1);
+    const int ky = it.v0 + l;
+    const int q = mx * mx + ky * ky;
+    if (q >= g.qlo && q < g.qhi) {
+      const int ix = mx < 0 ? mx + ng : mx;
+      buf[l * S + (mx < 0 ? mx + S : mx)] = spec ? spec[(long long)ix * hy + ky] : c_make<C>(T(1), T(0));
+    }
+  }
+  __syncthreads();
+  fft_lines<T>(buf, nl, S, a.st, tws, 1);
+  C* out = static_cast<C*>(a.g1) + g.g1_off;
+  for (int idx = threadIdx.x; idx < S * nl; idx += blockDim.x) {
+    const int l = idx % nl;
+    const int x = idx / nl;
+    out[(long long)x * r + it.v0 + l] = buf[l * S + x];
+  }
+}
+
 // ---------------------------------------------------------------- twiddles
 template <typename T>
 __global__ void twiddle_kernel(cplx<T>* tw, int ng) {
@@ -263,12 +306,18 @@ bsp_status launch_zpass(const PassArgs& a, int n_items, int lines, cudaStream_t 
   return launch_pass<T>(zpass_kernel<T>, a, n_items, lines, a.ngs / 2, s);
 }
 template <typename T>
+bsp_status launch_ring_xpass(const PassArgs& a, int n_items, int lines, cudaStream_t s) {
+  return launch_pass<T>(ring_xpass_kernel<T>, a, n_items, lines, a.ngs, s);
+}
+template <typename T>
 bsp_status launch_twiddles(void* tw, int ng, cudaStream_t s) {
   twiddle_kernel<T><<<(ng + 255) / 256, 256, 0, s>>>(static_cast<cplx<T>*>(tw), ng);
   BSP_CUDA(cudaGetLastError());
   return BSP_OK;
 }
 
+template bsp_status launch_ring_xpass<float>(const PassArgs&, int, int, cudaStream_t);
+template bsp_status launch_ring_xpass<double>(const PassArgs&, int, int, cudaStream_t);
 template bsp_status launch_xpass<float>(const PassArgs&, int, int, cudaStream_t);
 template bsp_status launch_xpass<double>(const PassArgs&, int, int, cudaStream_t);
 template bsp_status launch_ypass<float>(const PassArgs&, int, int, cudaStream_t);

@@ -137,6 +137,10 @@ template <typename T>
 bsp_status launch_ypass(const PassArgs& a, int n_items, int lines, cudaStream_t s);
 template <typename T>
 bsp_status launch_zpass(const PassArgs& a, int n_items, int lines, cudaStream_t s);
+// 2D rings: C2C along x of the (n, k_y) lines -> G[n][x][k_y < r] (the C2R along y is the Z
+// pass kernel run on those rows, see plan_passes_2d)
+template <typename T>
+bsp_status launch_ring_xpass(const PassArgs& a, int n_items, int lines, cudaStream_t s);
 template <typename T>
 bsp_status launch_twiddles(void* tw, int ng, cudaStream_t s);
 

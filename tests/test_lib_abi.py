@@ -40,13 +40,13 @@ def test_every_declared_symbol_is_exported(lib):
 P_EDGES = list(np.linspace(1.0, 8.0, 9))   # 8 shells up to Ng/4 at Ng = 32
 
 
-def _desc(lib_mod, edges, ng=32, prec=1, n_mu=10, n_t=10, rsd=0, beta=0.0, k1_merge=1, label_k=0, budget=0):
+def _desc(lib_mod, edges, ng=32, prec=1, n_mu=10, n_t=10, rsd=0, beta=0.0, k1_merge=1, label_k=0, budget=0, dim=0):
     e = np.ascontiguousarray(edges, dtype=np.float64)
     d = lib_mod.PlanDesc()
     d.ng, d.box_len, d.n_shells = ng, float(ng), len(e) - 1
     d.edges_kf = e.ctypes.data_as(C.POINTER(C.c_double))
     d.n_mu, d.n_t, d.rsd, d.beta, d.precision, d.mem_budget_bytes = n_mu, n_t, rsd, beta, prec, budget
-    d.k1_merge, d.label_k = k1_merge, label_k
+    d.k1_merge, d.label_k, d.dim = k1_merge, label_k, dim
     return d, e
 
 
@@ -62,6 +62,11 @@ def _desc(lib_mod, edges, ng=32, prec=1, n_mu=10, n_t=10, rsd=0, beta=0.0, k1_me
     (dict(edges=[1.0, 3.0], label_k=2), 1),
     (dict(edges=P_EDGES, budget=1000), 1),           # below one x-plane of the 8 shells (S = 24)
     (dict(edges=P_EDGES, prec=2, budget=100000), 6),  # split-BF16 fields do not stream in slabs
+    (dict(edges=P_EDGES, dim=5), 1),
+    (dict(edges=P_EDGES, dim=2, prec=2), 6),         # 2D plans: FP64 or FP32
+    (dict(edges=P_EDGES, dim=2, rsd=1), 6),
+    (dict(edges=[1.0, 3.0], dim=2, ng=8192), 6),
+    (dict(edges=[1.0, 5.0, 11.0], dim=2), 2),         # the cap after Eq. (2.12) holds in 2D too
 ])
 def test_argument_errors_without_gpu(lib, kw, status):
     from paper_2107_14564_gb300 import _lib
