@@ -48,6 +48,11 @@ WORKLOADS["ng768"] = dict(ng=768, box=768.0, n_index=1.5, f_ng=0.05, beta=None, 
                           n_mu=20, n_t=20, seed=7,
                           text="forward-only Ng=768 L=768 quadratic NG field P=k^-1.5 f=0.05, 24 linear shells "
                                "k_f..k_Nyq/2, 20x20 (mu,t) cells (run FP32, optionally under --mem-budget-gb)")
+WORKLOADS["fig_time"] = dict(text="timing against Ng (Sec. 2.2, Fig. 5): the equilateral bin of one ring (2D) or "
+                                  "shell (3D) with edges 29 and 31 k_f at Ng=384, L=215, both scaled with Ng at "
+                                  "fixed grid resolution (L = 215 Ng / 384); quadratic NG field P=k^-2 f=0.5",
+                             ng2d=(96, 192, 384, 768, 1536, 3072), ng3d=(96, 192, 288, 384, 512),
+                             dbe2d=(96, 192, 384, 768, 1536, 3072), seed=70)
 WORKLOADS["batch64"] = dict(text="64 seeded quadratic NG fields (P=k^-1.5, f=0.05) on uneven grids: 16 x 128^3, "
                                  "24 x 192^3, 24 x 256^3 (L=Ng), 16 linear shells k_f..k_Nyq/2 each, 10x10 "
                                  "(mu,t) cells, one captured CUDA graph",
@@ -454,6 +459,89 @@ def run_batch(args, w):
     batch.close()
 
 
+def run_fig_time(args, w):
+    """Fig. 5: FBE time of the equilateral bin against Ng in 2D and 3D (GPU, FP32 plans, CUDA
+    events), with the triangle count of the bin, and the direct summation (DBE) and the FBE of
+    the FP64 oracle on the host for 2D (the paper's single-core comparison)."""
+    import numpy as np
+    import torch
+    import fieldgen
+    from paper_2107_14564_gb300 import binding
+    rows = []
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(0)
+    clocks.start()
+    for dim, ngs in ((2, w["ng2d"]), (3, w["ng3d"])):
+        for ng in ngs:
+            sc = ng / 384.0
+            box, edges = 215.0 * sc, [29.0 * sc, 31.0 * sc]
+            if dim == 2:
+                spec = fieldgen.half_spectrum_c64(fieldgen.quadratic_field_2d(ng, box, 2.0, 0.5, w["seed"]))
+            else:
+                spec = fieldgen.half_spectrum_c64(fieldgen.quadratic_field(ng, box, 2.0, 0.5, w["seed"]))
+            plan = binding.Plan(ng, box, edges, 1, 1, precision="fp32", dim=dim)
+            if plan.n_triplets == 0:  # a ring this thin on this grid closes no triangle
+                log(f"[fig_time] {dim}D Ng={ng}: no closed triangle")
+                plan.close()
+                continue
+            sp = torch.from_numpy(spec).cuda()
+            for _ in range(args.warmup):
+                plan.estimate(sp, with_grid=False)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                plan.estimate(sp, with_grid=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            rows.append({"dim": dim, "ng": ng, "eval_grid": plan.ng_eval, "ntri": float(plan.triplets["ntri"][0]),
+                         "fbe_gpu_ms": e0.elapsed_time(e1) / args.steps})
+            log(f"[fig_time] {dim}D Ng={ng}: {rows[-1]}")
+            plan.close()
+            del sp
+    clk = clocks.stop()
+    # host side: the oracle's direct summation and FFT estimator of the same 2D bin (FP64)
+    from oracle import ring2d as R
+    cpu = []
+    for ng in w["dbe2d"]:
+        sc = ng / 384.0
+        box, edges = 215.0 * sc, [29.0 * sc, 31.0 * sc]
+        spec = fieldgen.spectrum(fieldgen.quadratic_field_2d(ng, box, 2.0, 0.5, w["seed"]))
+        pl = R.make_plan_2d(ng, box, edges, 1, 1)
+        t0 = time.perf_counter()
+        _, ntri = R.direct_estimate(spec, pl)
+        t1 = time.perf_counter()
+        if (0, 0, 0) in ntri:
+            R.estimate(spec, pl)
+        t2 = time.perf_counter()
+        cpu.append({"ng": ng, "ntri": ntri.get((0, 0, 0), 0), "dbe_s": t1 - t0, "fbe_s": t2 - t1})
+        log(f"[fig_time] oracle 2D Ng={ng}: {cpu[-1]}")
+
+    def slope(xs, ys):
+        return float(np.polyfit(np.log(xs), np.log(ys), 1)[0])
+
+    r2 = [r for r in rows if r["dim"] == 2]
+    r3 = [r for r in rows if r["dim"] == 3]
+    ref = next(r for r in r2 if r["ng"] == 384)
+    line = {"metric": "seconds for the equilateral bin of the largest ring against Ng (Fig. 5)",
+            "value": ref["fbe_gpu_ms"], "unit": "ms (2D FBE, Ng=384, GPU)", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ref["fbe_gpu_ms"], "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w["text"], "l2": "small grids fit L2: launch- and latency-bound"},
+            "rows": rows, "clocks": clk,
+            "slopes": {"ntri_2d": slope([r["ng"] for r in r2], [r["ntri"] for r in r2]),
+                       "ntri_3d": slope([r["ng"] for r in r3], [r["ntri"] for r in r3]),
+                       "dbe_2d_host": slope([c["ng"] for c in cpu if c["dbe_s"] > 0.05],
+                                            [c["dbe_s"] for c in cpu if c["dbe_s"] > 0.05]),
+                       "fbe_2d_gpu": slope([r["ng"] for r in r2], [r["fbe_gpu_ms"] for r in r2]),
+                       "fbe_3d_gpu": slope([r["ng"] for r in r3], [r["fbe_gpu_ms"] for r in r3])},
+            "cpu_baseline": {"kind": "oracle", "cores": os.cpu_count(), "rows": cpu,
+                             "sample": "direct summation and FP64 FFT estimator of the 2D bin, one run each"},
+            "roofline": None, "e2e": None}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -478,6 +566,8 @@ def main():
         run_reference(args, w)
     elif args.workload == "batch64":
         run_batch(args, w)
+    elif args.workload == "fig_time":
+        run_fig_time(args, w)
     else:
         run_ours(args, w)
 
