@@ -104,6 +104,14 @@ typedef struct {
                               [N_s][S][S], B = A_c^3 sum d d d / (A sum i i i) with the cell area
                               A_c = (L / Ng)^2 and A = L^2; BSP_FP64 or BSP_FP32 only, without RSD,
                               triangle-mean labels, memory budget, bsp_spectrum or bsp_grad. */
+  int order;               /* 0 or 3: the bispectrum. 4: the binned 4-point sum (trispectrum) that
+                              the FFT estimator extends to (Sec. 4: modes below 2 pi Ng / (4 L)):
+                              bins a >= b >= c >= e that can close, value V_c^4 sum_x d_a d_b d_c d_e
+                              / (V sum_x i_a i_b i_c i_e), N_tri the number of ordered closed
+                              quadrilaterals; it keeps the disconnected part (modes cancelling in
+                              pairs). BSP_FP64 or BSP_FP32, at most 16 shells, n_mu = n_t = 1, no
+                              memory budget or triangle-mean labels; bsp_contract and bsp_grad
+                              refuse it. */
 } bsp_plan_desc;
 
 /* One bin of triangles (Sec. 2.1): shells a >= b >= c and their labels (Eq. (2.4)). */
@@ -114,7 +122,9 @@ typedef struct {
   double ntri;         /* N_tri of Eq. (2.9)/(2.10), an integer, ordered triples */
   double tsum;         /* sum_x i_a i_b i_c = Ng^3 N_tri (FP64, as computed) */
   double k1, k2, k3;   /* lengths of sides a, b, c (units of k_f) per the plan's bsp_label_k */
-  double mu, t;        /* Eq. (2.4), unclamped */
+  double mu, t;        /* Eq. (2.4), unclamped (NaN for order-4 bins) */
+  int e;               /* order-4 bins: the fourth shell, a >= b >= c >= e; -1 otherwise */
+  int reserved;
 } bsp_triplet;
 
 typedef struct bsp_plan bsp_plan;

@@ -25,13 +25,15 @@ class PlanDesc(C.Structure):
                 ("mem_budget_bytes", C.c_size_t), ("autotune", C.c_int),
                 ("k1_merge", C.c_int),
                 ("label_k", C.c_int),
-                ("dim", C.c_int)]
+                ("dim", C.c_int),
+                ("order", C.c_int)]
 
 
 class Triplet(C.Structure):
     _fields_ = [("a", C.c_int), ("b", C.c_int), ("c", C.c_int), ("i_mu", C.c_int), ("i_t", C.c_int),
                 ("inside", C.c_int), ("ntri", C.c_double), ("tsum", C.c_double), ("k1", C.c_double),
-                ("k2", C.c_double), ("k3", C.c_double), ("mu", C.c_double), ("t", C.c_double)]
+                ("k2", C.c_double), ("k3", C.c_double), ("mu", C.c_double), ("t", C.c_double),
+                ("e", C.c_int), ("reserved", C.c_int)]
 
 
 class BispecError(RuntimeError):

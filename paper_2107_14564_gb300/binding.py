@@ -16,7 +16,8 @@ from ._lib import PRECISIONS, BispecError, PlanDesc, Triplet, check
 
 TRIPLET_DTYPE = np.dtype([("a", "i4"), ("b", "i4"), ("c", "i4"), ("i_mu", "i4"), ("i_t", "i4"),
                           ("inside", "i4"), ("ntri", "f8"), ("tsum", "f8"), ("k1", "f8"),
-                          ("k2", "f8"), ("k3", "f8"), ("mu", "f8"), ("t", "f8")])
+                          ("k2", "f8"), ("k3", "f8"), ("mu", "f8"), ("t", "f8"), ("e", "i4"),
+                          ("reserved", "i4")])
 
 
 def _stream_ptr(stream) -> int:
@@ -196,11 +197,12 @@ class Plan:
     forms (mu, t) from the shells' mean |k|, 'triangle' from the mean sides of each bin's
     triangles; mem_budget_bytes: the most bytes of shell fields to hold at once (0: all; else
     fields are produced and reduced x-slab by x-slab, see .slabs); dim: 3 for an Ng^3 cube in
-    spherical shells, 2 for an Ng^2 square in annular rings (spectrum [Ng, Ng/2+1])."""
+    spherical shells, 2 for an Ng^2 square in annular rings (spectrum [Ng, Ng/2+1]); order: 3 for
+    the bispectrum, 4 for the binned 4-point sum over bins a >= b >= c >= e (triplets["e"])."""
 
     def __init__(self, ng, box_len, edges_kf, n_mu=10, n_t=10, rsd=False, beta=0.0,
                  precision="fp32", stream=None, autotune=False, k1_merge=1,
-                 label_k="shell", mem_budget_bytes=0, dim=3):
+                 label_k="shell", mem_budget_bytes=0, dim=3, order=3):
         self._edges = np.ascontiguousarray(np.asarray(edges_kf, dtype=np.float64))
         desc = PlanDesc()
         desc.ng = int(ng)
@@ -219,6 +221,7 @@ class Plan:
             raise ValueError("label_k must be 'shell' or 'triangle'")
         desc.label_k = 0 if label_k == "shell" else 1
         desc.dim = int(dim)
+        desc.order = int(order)
         self.handle = None
         self.handle = bsp_plan_create(desc, stream)
         self.ng, self.box_len, self.n_mu, self.n_t = int(ng), float(box_len), int(n_mu), int(n_t)

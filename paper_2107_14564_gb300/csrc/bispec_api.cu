@@ -114,6 +114,9 @@ struct bsp_plan {
   int k1_merge = 1;         // k1 shells per (mu, t) cell group
   int label_k = BSP_LABEL_SHELL_MEAN;
   int dim = 3;              // 2: Ng^2 square with annular rings (Sec. 2.1); 3: Ng^3 cube with shells
+  int order = 3;            // 3: bispectrum; 4: binned 4-point sum over (a, b, c, e)
+  std::vector<int2> pairs4; // order 4: every shell pair (c, e), c >= e, in (c, e) order
+  int2* d_pairs4 = nullptr;
   size_t mem_budget = 0;    // bytes of shell fields the plan may hold at once (0: no limit)
   int slab_nx = 0;          // > 0: estimates stream x-slabs of this many planes of the evaluation grid
   std::vector<int> zi_off;  // generic Z items of slab k: [zi_off[k], zi_off[k + 1])
@@ -192,7 +195,12 @@ struct bsp_plan {
   int n_slabs() const { return slab_nx ? (ngs + slab_nx - 1) / slab_nx : 1; }
   int slab_x0(int k) const { return k * slab_nx; }
   int slab_len(int k) const { return slab_nx ? std::min(slab_nx, ngs - k * slab_nx) : ngs; }
-  size_t store_bytes() const { return (size_t)ns * (size_t)slab_len(0) * ngs * ngs * elem(); }  // p->fields
+  int n_extra() const { return order == 4 ? (int)pairs4.size() : 0; }  // product fields after the ns shells
+  int pid4(int c, int e) const { return c * (c + 1) / 2 + e; }         // index of (c, e) in pairs4
+  size_t store_bytes() const {                                           // p->fields
+    if (dim == 2 || order == 4) return (size_t)(ns + n_extra()) * (size_t)nvox() * elem();
+    return (size_t)ns * (size_t)slab_len(0) * ngs * ngs * elem();
+  }
 };
 
 struct bsp_batch {
@@ -415,6 +423,12 @@ int pick_gridx(const bsp_plan* p, int ntiles) { return pick_gridx_n(p->n_sm, nti
 bsp_status validate(const bsp_plan_desc* d) {
   if (!d) return fail(BSP_ERR_INVALID_ARG, "desc is NULL");
   if (d->dim != 0 && d->dim != 2 && d->dim != 3) return fail(BSP_ERR_INVALID_ARG, "dim must be 0, 2 or 3");
+  if (d->order != 0 && d->order != 3 && d->order != 4) return fail(BSP_ERR_INVALID_ARG, "order must be 0, 3 or 4");
+  if (d->order == 4) {
+    if (d->precision == BSP_MIXED_BF16X3 || d->n_shells > 16 || d->label_k != BSP_LABEL_SHELL_MEAN || d->mem_budget_bytes)
+      return fail(BSP_ERR_NOT_SUPPORTED, "order 4: FP64 or FP32, at most 16 shells, shell-mean labels, no memory budget");
+    if (d->n_mu != 1 || d->n_t != 1) return fail(BSP_ERR_INVALID_ARG, "order 4: n_mu = n_t = 1");
+  }
   if (d->dim == 2) {
     if (d->ng < 16 || d->ng > 4096 || (d->ng % 2) != 0)
       return fail(BSP_ERR_NOT_SUPPORTED, "2D: ng must be even and within [16, 4096]");
@@ -452,7 +466,8 @@ bsp_status validate(const bsp_plan_desc* d) {
 // S > 3 (r_max - 1) keeps only k = 0, exactly as the ng^3 grid does (the argument of Eq. (2.6) and
 // of the cap after Eq. (2.12)): sum over ng^3 = (ng / S)^3 sum over S^3, and the shell fields
 // sampled on the S grid are the same band-limited functions. The plan evaluates fields and
-// triple products on the smallest such S it has kernels for (at most ng).
+// triple products on the smallest such S it has kernels for (at most ng). A product of p fields
+// (order-p plans) needs S > p (r_max - 1) by the same argument.
 bool fft_size_ok(int n) {
   if (n < 16 || n % 8 != 0) return false;
   int m = n;
@@ -464,7 +479,7 @@ bool fft_size_ok(int n) {
 void choose_eval_grid(bsp_plan* p) {
   int rmax = 0;
   for (int n = 0; n < p->ns; ++n) rmax = std::max(rmax, (int)isqrt_ll(p->q[n + 1] - 1) + 1);
-  const int need = 3 * (rmax - 1) + 1;  // S >= need
+  const int need = p->order * (rmax - 1) + 1;  // S >= need (a product of `order` fields)
   int best = p->ng;
   for (int sz = 16; sz < p->ng; ++sz) {
     if (sz < need || !fft_size_ok(sz)) continue;
@@ -491,6 +506,7 @@ bsp_status host_plan(bsp_plan* p, const bsp_plan_desc* d) {
   p->k1_merge = d->k1_merge > 1 ? d->k1_merge : 1;
   p->label_k = d->label_k;
   p->dim = d->dim == 2 ? 2 : 3;
+  p->order = d->order == 4 ? 4 : 3;
   p->box_len = d->box_len;
   p->edges.assign(d->edges_kf, d->edges_kf + d->n_shells + 1);
   p->q.resize(p->ns + 1);
@@ -502,9 +518,10 @@ bsp_status host_plan(bsp_plan* p, const bsp_plan_desc* d) {
   for (int n = 0; n < p->ns; ++n)
     if (p->q[n + 1] <= p->q[n]) return fail(BSP_ERR_INVALID_ARG, "shell " + std::to_string(n) + " is empty");
   const long long qmax = p->q[p->ns];
-  // cap after Eq. (2.12): every mode |m| < Ng/3  <=>  9 (Q_Ns - 1) < Ng^2
-  if (9 * (qmax - 1) >= (long long)p->ng * p->ng)
-    return fail(BSP_ERR_ALIASING, "largest shell reaches k >= 2 pi Ng / (3 L)");
+  // cap after Eq. (2.12): every mode |m| < Ng/3  <=>  9 (Q_Ns - 1) < Ng^2; Ng / p for the
+  // order-p sum (Sec. 4)
+  if ((long long)p->order * p->order * (qmax - 1) >= (long long)p->ng * p->ng)
+    return fail(BSP_ERR_ALIASING, "largest shell reaches k >= 2 pi Ng / (" + std::to_string(p->order) + " L)");
   // mode counts per |m|^2
   const long long rr = isqrt_ll(qmax - 1);
   std::vector<long long> cnt(qmax, 0);
@@ -672,7 +689,7 @@ bsp_status build_levels(bsp_plan* p, cudaStream_t s) {
     }
     const int need = p->geom[p->trips[t].a].r + p->geom[p->trips[t].b].r + p->geom[cmax].r - 2;
     int g = S;
-    for (int cand = 16; cand < S && !p->slab_nx && p->dim == 3; cand += 8)  // x-slab and 2D plans: one level
+    for (int cand = 16; cand < S && !p->slab_nx && p->dim == 3 && p->order == 3; cand += 8)  // else one level
       if (S % cand == 0 && cand >= need) { g = cand; break; }
     std::vector<int>& v = bins_of(g);
     for (size_t w = t; w < u; ++w) v.push_back((int)w);
@@ -695,6 +712,7 @@ bsp_status build_levels(bsp_plan* p, cudaStream_t s) {
     std::vector<int> loc(p->ns, -1);
     if (L.top) {
       for (int n = 0; n < p->ns; ++n) { L.shells.push_back(n); loc[n] = n; }
+      for (int j = 0; j < p->n_extra(); ++j) L.shells.push_back(p->ns + j);  // order 4: pair products
     } else {
       std::vector<char> used(p->ns, 0);
       for (int b : L.bins) used[p->trips[b].a] = used[p->trips[b].b] = used[p->trips[b].c] = 1;
@@ -704,9 +722,10 @@ bsp_status build_levels(bsp_plan* p, cudaStream_t s) {
     const int nsh = (int)L.shells.size();
     std::vector<int> la, lb, lc;
     for (int b : L.bins) {
-      la.push_back(loc[p->trips[b].a]);
-      lb.push_back(loc[p->trips[b].b]);
-      lc.push_back(loc[p->trips[b].c]);
+      const bsp_triplet& t = p->trips[b];
+      la.push_back(loc[t.a]);
+      lb.push_back(loc[t.b]);
+      lc.push_back(p->order == 4 ? p->ns + p->pid4(t.c, t.e) : loc[t.c]);  // order 4: top level only
     }
     std::vector<int2> pairs;
     std::vector<Tile> tiles;
@@ -815,7 +834,7 @@ bsp_status build_levels(bsp_plan* p, cudaStream_t s) {
 bsp_status plan_sums(bsp_plan* p, bool lengths, const std::vector<int>& ca, const std::vector<int>& cb,
                      const std::vector<int>& cc, const std::vector<int>* ids, std::vector<double>& tsum,
                      cudaStream_t s) {
-  const int nf = lengths ? 2 * p->ns : p->ns;
+  const int nf = lengths ? 2 * p->ns : p->ns + p->n_extra();  // order 4: shell fields, then pair products
   const int S = p->ngs;
   const int lxy = fft_lines_for(S, BSP_FP64);
   const int lz = fft_lines_for(S / 2, BSP_FP64);
@@ -853,6 +872,9 @@ bsp_status plan_sums(bsp_plan* p, bool lengths, const std::vector<int>& ca, cons
   if (!slab) {
     TRY(run_passes<double>(p, nullptr, 0, tw, g1, g2, f, dxi, (int)xi.size(), dyi, (int)yi.size(), dzi,
                            (int)zi.size(), lxy, lz, s));
+    if (p->order == 4)
+      TRY(launch_pair_fields<double>(f, slab_vox, p->d_pairs4, p->n_extra(),
+                                     static_cast<double*>(f) + (size_t)p->ns * slab_vox, p->n_sm, s));
     if (lengths)
       TRY(run_passes<double>(p, nullptr, 0, tw, g1, g2, static_cast<double*>(f) + (size_t)p->ns * slab_vox,
                              dxi, (int)xi.size(), dyi, (int)yi.size(), dzi, (int)zi.size(), lxy, lz, s, 1));
@@ -1146,6 +1168,11 @@ bsp_status estimate_impl(bsp_plan* p, const void* spec, double* b_trip, double* 
   } else {
     st = plan_passes<T>(p, spec, p->fields, s, rec ? ev + 1 : nullptr, split);
     if (st != BSP_OK) return st;
+    if (p->order == 4) {  // product fields d_c d_e after the shell fields
+      st = launch_pair_fields<T>(p->fields, p->nvox(), p->d_pairs4, p->n_extra(),
+                                 static_cast<T*>(p->fields) + (size_t)p->ns * p->nvox(), p->n_sm, s);
+      if (st != BSP_OK) return st;
+    }
     st = run_contract<T>(p, p->fields, p->msum, s, rec ? ev[4] : nullptr, split && p->warp_fft);
     if (st != BSP_OK) return st;
   }
@@ -1157,7 +1184,7 @@ bsp_status estimate_impl(bsp_plan* p, const void* spec, double* b_trip, double* 
   f.cell_idx = p->cell_idx;
   f.n_cells = p->n_cells();
   const double vc = pow(p->box_len / p->ng, (double)p->dim);  // cell volume (area in 2D)
-  f.norm = vc * vc * vc / pow(p->box_len, (double)p->dim);
+  f.norm = pow(vc, (double)p->order) / pow(p->box_len, (double)p->dim);
   f.b_trip = b_trip;
   f.b_grid = b_grid;
   st = launch_finalize(f, s);
@@ -1172,7 +1199,8 @@ bsp_status estimate_impl(bsp_plan* p, const void* spec, double* b_trip, double* 
       const bool work = !p->levels.empty() && p->levels[0].ntiles > 0;
       p->launches += passes + 2LL * work * p->n_slabs() + 1;
     } else {
-      const int passes = p->warp_fft ? 3 : (p->nxi > 0) + (p->nyi > 0) + (p->nzi > 0) + (split ? 1 : 0);
+      const int passes = (p->warp_fft ? 3 : (p->nxi > 0) + (p->nyi > 0) + (p->nzi > 0) + (split ? 1 : 0)) +
+                         (p->order == 4);
       p->launches += passes + contract_launches(p) + 1;
     }
   }
@@ -1350,21 +1378,37 @@ bsp_status bsp_plan_create(const bsp_plan_desc* desc, void* stream, bsp_plan** o
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->n_sm, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) { delete p; return cuda_fail(e, "device query"); }
-  // candidate bins: the triangle inequality on the extreme mode lengths
-  std::vector<int> ca, cb, cc;
+  // candidate bins: the triangle inequality on the extreme mode lengths (order 4: the largest
+  // side of a closed quadrilateral is at most the sum of the others); an order-4 bin (a, b, c, e)
+  // is summed as the triple (a, b, ns + pid4(c, e)) of shell fields and pair-product fields
+  std::vector<int> ca, cb, cc, c4;
+  auto qmaxr = [&](int n) { return sqrt((double)(p->q[n + 1] - 1)); };
   for (int a = 0; a < p->ns; ++a)
     for (int b = 0; b <= a; ++b)
       for (int c = 0; c <= b; ++c) {
-        const double qa = (double)p->q[a];
-        const double qb = (double)(p->q[b + 1] - 1);
-        const double qc = (double)(p->q[c + 1] - 1);
-        if (sqrt(qa) <= sqrt(qb) + sqrt(qc)) { ca.push_back(a); cb.push_back(b); cc.push_back(c); }
+        const double ra = sqrt((double)p->q[a]);
+        if (p->order == 3) {
+          if (ra <= qmaxr(b) + qmaxr(c)) { ca.push_back(a); cb.push_back(b); cc.push_back(c); c4.push_back(-1); }
+          continue;
+        }
+        for (int e = 0; e <= c; ++e)
+          if (ra <= qmaxr(b) + qmaxr(c) + qmaxr(e)) {
+            ca.push_back(a); cb.push_back(b); cc.push_back(c); c4.push_back(e);
+          }
       }
   // geometry on the device (shared by the FP64 count and the estimator)
   st = dev_upload(p, p->geom, &p->d_geom, s);
   if (st != BSP_OK) { bsp_plan_destroy(p); return st; }
+  std::vector<int> cc_sum = cc;  // the third index of each candidate's triple sum
+  if (p->order == 4) {
+    for (int c = 0; c < p->ns; ++c)
+      for (int e = 0; e <= c; ++e) p->pairs4.push_back(make_int2(c, e));
+    st = dev_upload(p, p->pairs4, &p->d_pairs4, s);
+    if (st != BSP_OK) { bsp_plan_destroy(p); return st; }
+    for (size_t i = 0; i < cc.size(); ++i) cc_sum[i] = p->ns + p->pid4(cc[i], c4[i]);
+  }
   std::vector<double> tsum;
-  st = plan_sums(p, false, ca, cb, cc, nullptr, tsum, s);
+  st = plan_sums(p, false, ca, cb, cc_sum, nullptr, tsum, s);
   if (st != BSP_OK) { bsp_plan_destroy(p); return st; }
   for (double& t : tsum) t *= p->sum_scale;  // sums over the ng^3 grid (exact up to rounding)
   const double ng3 = p->dim == 2 ? (double)p->ng * (double)p->ng : (double)p->ng * (double)p->ng * (double)p->ng;
@@ -1376,13 +1420,14 @@ bsp_status bsp_plan_create(const bsp_plan_desc* desc, void* stream, bsp_plan** o
     if (fabs(nt - rn) > 1e-3) {
       bsp_plan_destroy(p);
       return fail(BSP_ERR_NUMERIC, "non-integral triangle count for bin (" + std::to_string(ca[i]) + "," +
-                                       std::to_string(cb[i]) + "," + std::to_string(cc[i]) + ")");
+                                       std::to_string(cb[i]) + "," + std::to_string(cc[i]) +
+                                       (c4[i] >= 0 ? "," + std::to_string(c4[i]) : std::string()) + ")");
     }
     if (rn <= 0.0) continue;
     ka.push_back(ca[i]); kb.push_back(cb[i]); kc.push_back(cc[i]);
     kt.push_back(tsum[i]);
     bsp_triplet t{};
-    t.a = ca[i]; t.b = cb[i]; t.c = cc[i];
+    t.a = ca[i]; t.b = cb[i]; t.c = cc[i]; t.e = c4[i];
     t.ntri = rn;
     t.tsum = tsum[i];
     t.k1 = p->kbar[t.a]; t.k2 = p->kbar[t.b]; t.k3 = p->kbar[t.c];
@@ -1417,6 +1462,11 @@ bsp_status bsp_plan_create(const bsp_plan_desc* desc, void* stream, bsp_plan** o
     }
   }
   for (bsp_triplet& t : p->trips) {  // Eq. (2.4) and the (mu, t) cell
+    if (p->order == 4) {  // no triangle shape: every bin in the one cell of its k1 group
+      t.mu = t.t = NAN;
+      t.i_mu = t.i_t = t.inside = 0;
+      continue;
+    }
     const double k1 = t.k1, k2 = t.k2, k3 = t.k3;
     t.t = k2 / k1;
     t.mu = 0.5 * (k1 / k2 + k2 / k1 - (k3 / k1) * (k3 / k2));
@@ -1544,6 +1594,7 @@ bsp_status bsp_shell_fields(bsp_plan* p, const void* spec, void* fields_out, voi
 bsp_status bsp_contract(bsp_plan* p, const void* fields, double* msum, void* stream) {
   if (!p || !fields || !msum) return fail(BSP_ERR_INVALID_ARG, "NULL argument");
   if ((reinterpret_cast<uintptr_t>(fields) & 15) != 0) return fail(BSP_ERR_INVALID_ARG, "fields must be 16-byte aligned");
+  if (p->order == 4) return fail(BSP_ERR_NOT_SUPPORTED, "bsp_contract: order-4 plans sum pair-product fields");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (p->prec == BSP_FP64) return run_contract<double>(p, fields, msum, s, nullptr);
   if (p->prec == BSP_MIXED_BF16X3) {
@@ -1786,7 +1837,8 @@ bsp_status bsp_spectrum(bsp_plan* p, const float* delta_x, void* spec_out, void*
 
 bsp_status bsp_grad(bsp_plan* p, const void* spec, const double* dl_db, float* dl_ddelta, void* stream) {
   if (!p || !spec || !dl_db || !dl_ddelta) return fail(BSP_ERR_INVALID_ARG, "NULL argument");
-  if (p->prec == BSP_FP64 || p->dim == 2) return fail(BSP_ERR_NOT_SUPPORTED, "bsp_grad needs a 3D FP32 or mixed plan");
+  if (p->prec == BSP_FP64 || p->dim == 2 || p->order == 4)
+    return fail(BSP_ERR_NOT_SUPPORTED, "bsp_grad needs a 3D bispectrum plan in FP32 or mixed precision");
   if (!warp_fft_supported(p->ngs) || !warp_fft_supported(p->ng))
     return fail(BSP_ERR_NOT_SUPPORTED, "bsp_grad needs grid sides 2^p or 3 * 2^p in [128, 1024]");
   cudaStream_t s = static_cast<cudaStream_t>(stream);

@@ -124,6 +124,34 @@ bsp_status launch_reduce_partials(const ContractArgs& a, cudaStream_t s) {
   return BSP_OK;
 }
 
+// ---------------------------------------------------------------- product fields (order 4)
+template <typename T>
+__global__ void pair_fields_kernel(const T* __restrict__ f, long long nvox, const int2* __restrict__ pairs, int np,
+                                   T* __restrict__ out) {
+  const long long total = nvox * np;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(i / nvox);
+    const long long v = i - (long long)j * nvox;
+    const int2 ab = pairs[j];
+    out[i] = f[(long long)ab.x * nvox + v] * f[(long long)ab.y * nvox + v];
+  }
+}
+
+template <typename T>
+bsp_status launch_pair_fields(const void* f, long long nvox, const int2* pairs, int np, void* out, int n_sm,
+                              cudaStream_t s) {
+  if (np == 0 || nvox == 0) return BSP_OK;
+  const long long need = (nvox * np + 255) / 256;
+  const long long blocks = std::min<long long>(need, 8LL * std::max(n_sm, 1));
+  pair_fields_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(static_cast<const T*>(f), nvox, pairs, np,
+                                                         static_cast<T*>(out));
+  BSP_CUDA(cudaGetLastError());
+  return BSP_OK;
+}
+
+template bsp_status launch_pair_fields<float>(const void*, long long, const int2*, int, void*, int, cudaStream_t);
+template bsp_status launch_pair_fields<double>(const void*, long long, const int2*, int, void*, int, cudaStream_t);
 template bsp_status launch_contract_simt<float>(const ContractArgs&, cudaStream_t);
 template bsp_status launch_contract_simt<double>(const ContractArgs&, cudaStream_t);
 

@@ -137,6 +137,11 @@ template <typename T>
 bsp_status launch_ypass(const PassArgs& a, int n_items, int lines, cudaStream_t s);
 template <typename T>
 bsp_status launch_zpass(const PassArgs& a, int n_items, int lines, cudaStream_t s);
+// out[j][v] = f[pairs[j].x][v] * f[pairs[j].y][v] for v < nvox (order-4 plans: the product fields
+// d_c d_e through which sum_x d_a d_b d_c d_e becomes a triple sum)
+template <typename T>
+bsp_status launch_pair_fields(const void* f, long long nvox, const int2* pairs, int np, void* out, int n_sm,
+                              cudaStream_t s);
 // 2D rings: C2C along x of the (n, k_y) lines -> G[n][x][k_y < r] (the C2R along y is the Z
 // pass kernel run on those rows, see plan_passes_2d)
 template <typename T>

@@ -40,13 +40,13 @@ def test_every_declared_symbol_is_exported(lib):
 P_EDGES = list(np.linspace(1.0, 8.0, 9))   # 8 shells up to Ng/4 at Ng = 32
 
 
-def _desc(lib_mod, edges, ng=32, prec=1, n_mu=10, n_t=10, rsd=0, beta=0.0, k1_merge=1, label_k=0, budget=0, dim=0):
+def _desc(lib_mod, edges, ng=32, prec=1, n_mu=10, n_t=10, rsd=0, beta=0.0, k1_merge=1, label_k=0, budget=0, dim=0, order=0):
     e = np.ascontiguousarray(edges, dtype=np.float64)
     d = lib_mod.PlanDesc()
     d.ng, d.box_len, d.n_shells = ng, float(ng), len(e) - 1
     d.edges_kf = e.ctypes.data_as(C.POINTER(C.c_double))
     d.n_mu, d.n_t, d.rsd, d.beta, d.precision, d.mem_budget_bytes = n_mu, n_t, rsd, beta, prec, budget
-    d.k1_merge, d.label_k, d.dim = k1_merge, label_k, dim
+    d.k1_merge, d.label_k, d.dim, d.order = k1_merge, label_k, dim, order
     return d, e
 
 
@@ -67,6 +67,10 @@ def _desc(lib_mod, edges, ng=32, prec=1, n_mu=10, n_t=10, rsd=0, beta=0.0, k1_me
     (dict(edges=P_EDGES, dim=2, rsd=1), 6),
     (dict(edges=[1.0, 3.0], dim=2, ng=8192), 6),
     (dict(edges=[1.0, 5.0, 11.0], dim=2), 2),         # the cap after Eq. (2.12) holds in 2D too
+    (dict(edges=P_EDGES, order=5), 1),
+    (dict(edges=[1.0, 4.0, 7.0], order=4, n_mu=1, n_t=1, prec=2), 6),
+    (dict(edges=[1.0, 4.0, 7.0], order=4), 1),              # order 4: one (mu, t) cell
+    (dict(edges=[1.0, 4.0, 10.0], order=4, n_mu=1, n_t=1), 2),  # below Ng/3 but not below Ng/4
 ])
 def test_argument_errors_without_gpu(lib, kw, status):
     from paper_2107_14564_gb300 import _lib
@@ -100,3 +104,23 @@ def test_plan_desc_layout_matches_the_header():
             names += [re.sub(r"[\s\*]", "", n.split()[-1] if i == 0 else n)
                       for i, n in enumerate(decl.split(","))]
     assert names == [f[0] for f in _lib.PlanDesc._fields_]
+
+
+def _struct_fields(name):
+    txt = open(os.path.join(ROOT, "include", "bispec.h")).read()
+    body = re.search(r"typedef struct \{([^{}]*)\} " + name + ";", txt).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    names = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if decl:
+            names += [re.sub(r"[\s\*]", "", n.split()[-1] if i == 0 else n) for i, n in enumerate(decl.split(","))]
+    return names
+
+
+def test_triplet_layout_matches_the_header():
+    """The binding's Triplet and its numpy dtype list bsp_triplet's fields in the header's order."""
+    from paper_2107_14564_gb300 import _lib, binding
+    names = _struct_fields("bsp_triplet")
+    assert names == [f[0] for f in _lib.Triplet._fields_] == list(binding.TRIPLET_DTYPE.names)
+    assert C.sizeof(_lib.Triplet) == binding.TRIPLET_DTYPE.itemsize
