@@ -53,7 +53,7 @@ typedef enum {
   BSP_ERR_OOM = 3,           /* a device or host allocation failed */
   BSP_ERR_CUDA = 4,          /* a CUDA runtime or launch error */
   BSP_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up */
-  BSP_ERR_NOT_SUPPORTED = 6, /* a grid size or option this build does not handle */
+  BSP_ERR_NOT_SUPPORTED = 6, /* a grid size or option the library does not handle */
   BSP_ERR_NUMERIC = 7        /* a triangle count came out non-integral (Eq. (2.10)) */
 } bsp_status;
 
