@@ -397,7 +397,8 @@ def run_ours(args, w):
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(nlaunch.value), "clocks": clk,
             "stages": stages, "plan_seconds": round(plan_s, 2), "plain_fp32": plain,
             "eval_grid": plan.ng_eval, "contraction_levels": plan.tuning,
-            "device_bytes": plan.device_bytes, "x_slabs": list(plan.slabs)}
+            "device_bytes": plan.device_bytes, "x_slabs": list(plan.slabs),
+            "fft_grid_blocks": {"ypass": plan.pass_tuning[0], "zpass": plan.pass_tuning[1]}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     plan.close()

@@ -94,7 +94,10 @@ typedef struct {
   int autotune;            /* 1: at creation, time the tensor-core contraction of every level with
                               its voxels split over 1, 2 and 4 x (SM count) blocks per M tile and
                               keep the fastest (BSP_MIXED_BF16X3 plans; the split changes only the
-                              order of the FP64 cross-block sums). No counterpart in the paper. */
+                              order of the FP64 cross-block sums), and time the persistent Y and Z
+                              FFT passes with grids of 1 .. 16 x (SM count) blocks and keep the
+                              fastest (FP32 and mixed plans on the warp passes; the grid changes no
+                              value). No counterpart in the paper. */
   int k1_merge;            /* (mu, t) cells span this many neighbouring k1 shells (Sec. 2.1, last
                               paragraph: merging adjacent bins); 0 or 1: one shell per cell group */
   int label_k;             /* a bsp_label_k: the lengths the labels (mu, t) are formed from */
@@ -279,6 +282,9 @@ BSP_API bsp_status bsp_plan_stage_work(const bsp_plan* plan, double* bytes, doub
 
 /* Bytes bsp_estimate_host copies host->device per call (the spectrum box of the outermost shell). */
 BSP_API bsp_status bsp_plan_host_input_bytes(const bsp_plan* plan, size_t* bytes);
+
+/* Grids of the persistent Y and Z FFT passes the autotuner picked (0: as many blocks as fit). */
+BSP_API bsp_status bsp_plan_pass_tuning(const bsp_plan* plan, int* y_blocks, int* z_blocks);
 
 /* The x-slabs an estimate streams under mem_budget_bytes: slab_planes x-planes of the evaluation
  * grid per slab (the last one may be thinner) and n_slabs of them; 0 and 1 when the plan holds

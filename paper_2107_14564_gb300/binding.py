@@ -53,6 +53,13 @@ def bsp_plan_grid(handle) -> int:
     return n.value
 
 
+def bsp_plan_pass_tuning(handle):
+    """(Y-pass blocks, Z-pass blocks) the autotuner picked; 0 = as many as fit."""
+    y, z = C.c_int(), C.c_int()
+    check(_lib.load().bsp_plan_pass_tuning(handle, C.byref(y), C.byref(z)))
+    return y.value, z.value
+
+
 def bsp_plan_slabs(handle):
     """(x-planes per slab, number of slabs) an estimate streams; (0, 1) without a memory budget."""
     planes, n = C.c_int(), C.c_int()
@@ -237,6 +244,7 @@ class Plan:
         self.tuning = bsp_plan_tuning(self.handle)
         self.host_input_bytes = bsp_plan_host_input_bytes(self.handle)
         self.slabs = bsp_plan_slabs(self.handle)
+        self.pass_tuning = bsp_plan_pass_tuning(self.handle)
 
     def close(self):
         if self.handle is not None:
@@ -315,5 +323,5 @@ class Plan:
 
 
 __all__ = ["Plan", "BispecError", "bsp_plan_create", "bsp_plan_destroy", "bsp_plan_info",
-           "bsp_plan_triplets", "bsp_plan_grid", "bsp_plan_tuning", "bsp_plan_host_input_bytes", "bsp_plan_slabs", "bsp_shell_fields", "bsp_contract", "bsp_estimate",
+           "bsp_plan_triplets", "bsp_plan_grid", "bsp_plan_tuning", "bsp_plan_host_input_bytes", "bsp_plan_slabs", "bsp_plan_pass_tuning", "bsp_shell_fields", "bsp_contract", "bsp_estimate",
            "bsp_estimate_host", "bsp_estimate_batched", "Batch", "bsp_spectrum", "bsp_grad", "bsp_last_sums", "bsp_plan_check", "bsp_version", "TRIPLET_DTYPE"]

@@ -111,6 +111,7 @@ struct bsp_plan {
   // description
   int ng = 0, ns = 0, n_mu = 0, n_t = 0, rsd = 0, prec = 0;
   int autotune = 0;
+  int y_blocks = 0, z_blocks = 0;  // warp Y and Z pass grids picked by autotune_passes (0: as many as fit)
   int k1_merge = 1;         // k1 shells per (mu, t) cell group
   int label_k = BSP_LABEL_SHELL_MEAN;
   int dim = 3;              // 2: Ng^2 square with annular rings (Sec. 2.1); 3: Ng^3 cube with shells
@@ -667,6 +668,58 @@ bsp_status autotune_levels(bsp_plan* p, cudaStream_t s) {
   return st;
 }
 
+// FFT pass autotuner (plans created with autotune = 1 on the warp passes): the persistent Y and Z
+// passes are timed on the plan's own buffers (a zero spectrum; the work does not depend on the
+// values) with grids of 1, 2, 3, 4, 6, 8, 12 and 16 x (SM count) blocks and as many as fit, 3 launches
+// after one warm-up each, and the fastest grid is kept. The grid changes only which block takes
+// which lines, not what any line computes.
+// Which passes plan_passes launches: all three over the whole grid, the X and Y passes only, or
+// (a value k >= 0) the Z pass of x-slab k, its fields laid out [n][x - x0][y][z] in `fields`.
+constexpr int kPassAll = -1;
+constexpr int kPassXY = -2;
+template <typename T>
+bsp_status plan_passes(bsp_plan* p, const void* spec, void* fields, cudaStream_t s, cudaEvent_t* ev,
+                       bool split = false, int part = kPassAll);
+bsp_status autotune_passes(bsp_plan* p, cudaStream_t s) {
+  if (!p->warp_fft) return BSP_OK;
+  void* spec = nullptr;
+  bsp_status st = dev_alloc(p, p->spec_bytes(), &spec);
+  if (st != BSP_OK) return st;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t ce = cudaMemsetAsync(spec, 0, p->spec_bytes(), s);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+  if (ce != cudaSuccess) st = cuda_fail(ce, "pass autotuner setup");
+  const bool split = p->prec == BSP_MIXED_BF16X3;
+  const int mults[] = {0, 1, 2, 3, 4, 6, 8, 12, 16};  // 0: as many as fit
+  int* knob[2] = {&p->y_blocks, &p->z_blocks};
+  for (int pass = 0; pass < 2 && st == BSP_OK; ++pass) {
+    float best = 1e30f;
+    int best_blocks = 0;
+    for (int m : mults) {
+      *knob[pass] = m * p->n_sm;
+      // warm-up (the Y pass needs the X pass output once; the Z pass reads what Y wrote)
+      if ((st = plan_passes<float>(p, spec, p->fields, s, nullptr, split, kPassAll)) != BSP_OK) break;
+      if ((ce = cudaEventRecord(e0, s)) != cudaSuccess) { st = cuda_fail(ce, "cudaEventRecord"); break; }
+      for (int r = 0; r < 3 && st == BSP_OK; ++r) st = plan_passes<float>(p, spec, p->fields, s, nullptr, split, kPassAll);
+      if (st != BSP_OK) break;
+      if ((ce = cudaEventRecord(e1, s)) != cudaSuccess || (ce = cudaEventSynchronize(e1)) != cudaSuccess) {
+        st = cuda_fail(ce, "pass autotune timing");
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) { best = ms; best_blocks = *knob[pass]; }
+    }
+    *knob[pass] = best_blocks;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaStreamSynchronize(s);
+  dev_free(p, spec);
+  return st;
+}
+
 // Contraction levels (see ContractLevel): each pair (a, b) of the kept bins goes to the smallest
 // divisor g of the evaluation grid (g % 8 == 0, g >= 16) above r_a + r_b + r_cmax - 3, the largest
 // wavevector component of its triple products.
@@ -1039,17 +1092,12 @@ bsp_status contract_slab(bsp_plan* p, int k, cudaStream_t s) {
   return launch_reduce_partials(c, s);
 }
 
-// Which passes plan_passes launches: all three over the whole grid, the X and Y passes only, or
-// (a value k >= 0) the Z pass of x-slab k, its fields laid out [n][x - x0][y][z] in `fields`.
-constexpr int kPassAll = -1;
-constexpr int kPassXY = -2;
-
 // The pass launches of an estimate on the plan's buffers; ev (optional) receives an event after
 // the X and after the Y pass, and after the Z pass. split: write split fields (the layout of the
 // tensor-core contraction, see TcArgs) instead of FP32 ones.
 template <typename T>
-bsp_status plan_passes(bsp_plan* p, const void* spec, void* fields, cudaStream_t s, cudaEvent_t* ev, bool split = false,
-                       int part = kPassAll) {
+bsp_status plan_passes(bsp_plan* p, const void* spec, void* fields, cudaStream_t s, cudaEvent_t* ev, bool split,
+                       int part) {
   PassArgs a{};
   a.n_sm = p->n_sm;
   a.spec = spec;
@@ -1079,11 +1127,13 @@ bsp_status plan_passes(bsp_plan* p, const void* spec, void* fields, cudaStream_t
       if (st != BSP_OK) return st;
       if (ev) BSP_CUDA(cudaEventRecord(ev[0], s));
       a.items = p->d_wyi;
+      a.grid_blocks = p->y_blocks;
       st = launch_warp_ypass(a, p->nwyi, s);
       if (st != BSP_OK) return st;
       if (ev) BSP_CUDA(cudaEventRecord(ev[1], s));
       if (part == kPassXY) return BSP_OK;
     }
+    a.grid_blocks = p->z_blocks;
     long long lines = (long long)p->ns * p->ngs * p->ngs;
     if (part >= 0) {
       a.slab_x0 = p->slab_x0(part);
@@ -1523,6 +1573,7 @@ bsp_status bsp_plan_create(const bsp_plan_desc* desc, void* stream, bsp_plan** o
   TRY(dev_alloc(p, p->store_bytes(), &p->fields));  // all fields, or one x-slab of them
   if (p->prec == BSP_MIXED_BF16X3 && !p->warp_fft) TRY(dev_alloc(p, p->field_bytes(), &p->fields32));
   TRY(build_levels(p, s));
+  if (p->autotune) TRY(autotune_passes(p, s));
   void* tmp = nullptr;
   TRY(dev_alloc(p, std::max<size_t>(p->trips.size(), 1) * sizeof(double), &tmp));
   p->msum = static_cast<double*>(tmp);
@@ -1746,6 +1797,13 @@ bsp_status bsp_estimate_host(bsp_plan* p, const void* spec_host, double* b_tripl
     BSP_CUDA(cudaMemcpyAsync(b_grid_host, p->bgrid_dev, (size_t)p->n_cells() * sizeof(double),
                              cudaMemcpyDeviceToHost, s));
   BSP_CUDA(cudaStreamSynchronize(s));
+  return BSP_OK;
+}
+
+bsp_status bsp_plan_pass_tuning(const bsp_plan* p, int* y_blocks, int* z_blocks) {
+  if (!p || !y_blocks || !z_blocks) return fail(BSP_ERR_INVALID_ARG, "NULL argument");
+  *y_blocks = p->y_blocks;
+  *z_blocks = p->z_blocks;
   return BSP_OK;
 }
 

@@ -609,6 +609,7 @@ bsp_status launch_xy(const PassArgs& a, int n_items, int n_sm, cudaStream_t s) {
     int per_sm = 0;
     BSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, xy_warp_kernel<N, XPASS>, XY<N>::kThreads, smem));
     blocks = std::min<long long>((long long)std::max(per_sm, 1) * std::max(n_sm, 1), n_items);
+    if (a.grid_blocks > 0) blocks = std::min<long long>(a.grid_blocks, n_items);
   }
   xy_warp_kernel<N, XPASS><<<(unsigned)blocks, XY<N>::kThreads, smem, s>>>(a, n_items);
   BSP_CUDA(cudaGetLastError());
@@ -628,6 +629,7 @@ bsp_status launch_z(const PassArgs& a, long long n_lines, int n_sm, cudaStream_t
   BSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kZThreads, smem));
   long long blocks = (long long)std::max(per_sm, 1) * n_sm;
   const long long need = (n_lines + (kZThreads / 32) * LPW - 1) / ((kZThreads / 32) * LPW);
+  if (a.grid_blocks > 0) blocks = a.grid_blocks;
   if (blocks > need) blocks = need;
   if (blocks < 1) blocks = 1;
   kern<<<(unsigned)blocks, kZThreads, smem, s>>>(a, n_lines);

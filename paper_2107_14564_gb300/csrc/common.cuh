@@ -74,6 +74,7 @@ struct PassArgs {
   int rsd;
   double beta;
   int kweight;            // generic X pass, counting input only: mode value |k| / k_f instead of 1
+  int grid_blocks;        // warp Y and Z passes: blocks of the persistent grid (0: as many as fit)
   int slab_x0, slab_nx;   // Z passes: only x in [slab_x0, slab_x0 + slab_nx) of the evaluation grid,
                           // fields laid out [n][x - slab_x0][y][z]; slab_nx = 0: the whole grid
   FftStages st;           // stage list of this pass's line length

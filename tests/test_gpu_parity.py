@@ -232,6 +232,10 @@ def test_autotuned_plan_matches(lib):
     b.check()
     assert np.max(np.abs(ba - bb) / res["b_scale"]) < 1e-5
     assert np.max(_cond_err(bb, res)) < 1e-4
+    # the FFT pass grids change no value: the shell fields are the same bits
+    assert a.pass_tuning == (0, 0) and all(v % torch.cuda.get_device_properties(0).multi_processor_count == 0
+                                           for v in b.pass_tuning)
+    assert torch.equal(a.shell_fields(d), b.shell_fields(d))
 
 
 def test_host_entry_reads_only_the_shell_box(lib):
