@@ -121,6 +121,7 @@ struct Tile { int p0, np, c0, pad; };
 
 // ---------------------------------------------------------------- error handling
 void set_error(const std::string& msg);
+void set_error_c(const char* msg);  // no allocation
 bsp_status fail(bsp_status s, const std::string& msg);
 bsp_status fail_c(bsp_status s, const char* msg);  // no allocation
 bsp_status cuda_fail(cudaError_t e, const char* what);
