@@ -822,7 +822,6 @@ bsp_status bsp_plan_create(const bsp_plan_desc* desc, void* stream, bsp_plan** o
   if (st != BSP_OK) { bsp_plan_destroy(p); return st; }
   for (double& t : tsum) t *= p->sum_scale;  // sums over the ng^3 grid (exact up to rounding)
   const double ng3 = p->dim == 2 ? (double)p->ng * (double)p->ng : (double)p->ng * (double)p->ng * (double)p->ng;
-  std::vector<int> ka, kb, kc;
   std::vector<double> kt;
   for (size_t i = 0; i < ca.size(); ++i) {
     const double nt = tsum[i] / ng3;
@@ -834,7 +833,6 @@ bsp_status bsp_plan_create(const bsp_plan_desc* desc, void* stream, bsp_plan** o
                                        (c4[i] >= 0 ? "," + std::to_string(c4[i]) : std::string()) + ")");
     }
     if (rn <= 0.0) continue;
-    ka.push_back(ca[i]); kb.push_back(cb[i]); kc.push_back(cc[i]);
     kt.push_back(tsum[i]);
     bsp_triplet t{};
     t.a = ca[i]; t.b = cb[i]; t.c = cc[i]; t.e = c4[i];
