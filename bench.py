@@ -240,6 +240,29 @@ def config_of(w, precision):
                   "than the 129 MB L2"}
 
 
+# ------------------------------------------------------------------ replicas over ranks
+def rank_seed(seed, rank):
+    """Each rank estimates its own independently seeded field (replicas, no data exchange)."""
+    return seed + 1000 * rank
+
+
+def max_over_ranks(x, dist):
+    """The largest x over all ranks (x itself without a process group): the job's time is the
+    slowest rank's."""
+    if dist is None:
+        return x
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, ms_max):
+    """Whole-job throughput: the units all ranks processed per second of the slowest rank."""
+    return units_per_rank * world / (ms_max / 1000.0)
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_ours(args, w):
     import numpy as np
@@ -254,7 +277,7 @@ def run_ours(args, w):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    spec_np = make_input(w, w["seed"] + 1000 * rank)
+    spec_np = make_input(w, rank_seed(w["seed"], rank))
     spec = torch.from_numpy(spec_np).cuda()
     t0 = time.perf_counter()
     plan = binding.Plan(w["ng"], w["box"], edges_of(w), w["n_mu"], w["n_t"],
@@ -295,14 +318,10 @@ def run_ours(args, w):
     wb = (C.c_double * 5)()
     wf = (C.c_double * 5)()
     _lib.check(lib.bsp_plan_stage_work(plan.handle, wb, wf))
-    ms_max = ms
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, dist)
     bins = plan.n_triplets * world
-    value = bins / (ms_max / 1000.0)
-    fields_per_s = plan.n_shells * world / (ms_max / 1000.0)
+    value = job_rate(plan.n_triplets, world, ms_max)
+    fields_per_s = job_rate(plan.n_shells, world, ms_max)
 
     # end to end through the host-buffer entry point
     pinned = torch.from_numpy(spec_np).pin_memory()
@@ -312,11 +331,7 @@ def run_ours(args, w):
     t0 = time.perf_counter()
     for _ in range(args.steps):
         plan.estimate_host(pinned)
-    e2e_s = (time.perf_counter() - t0) / args.steps
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, dist)
     e2e = {"value": bins / e2e_s, "unit": "bins/s",
            "h2d_bytes_per_step": int(plan.host_input_bytes),  # the spectrum box the shells reach
            "d2h_bytes_per_step": int(8 * (plan.n_triplets + plan.n_groups * w["n_mu"] * w["n_t"]))}
