@@ -83,7 +83,7 @@ def test_autograd_function_loss(lib):
 
 
 @pytest.mark.slow
-def test_adjoint_config5_sampled_voxels(lib):
+def test_adjoint_ng256_24_shells_sampled_voxels(lib):
     """Ng=256, 24 shells up to k_Nyq/2, FP32: the adjoint at 64 seeded voxels against the oracle."""
     ng = 256
     _, delta, gp, pl = _setup(lib, ng, 24, 64.0, 5)

@@ -52,7 +52,7 @@ def _check_plan_tables(gp, res, pl):
     assert np.array_equal(tr["k1"], pl.kbar[tr["a"]])
 
 
-def test_fp64_config1_parity(lib):
+def test_fp64_ng32_8_shells_parity(lib):
     """Ng=32, L=32, 8 linear shells k_f..k_Nyq/2, P=k^-2, f=0.1, 10x10 cells, FP64: 1e-10."""
     ng = 32
     edges = _edges(ng, 8)
