@@ -87,3 +87,39 @@ def test_forward_of_adjoint_matches_estimator():
     b1 = G.estimate_real(delta, pl, trips, tsum)
     b2 = fbe.estimate(fieldgen.spectrum(delta), pl, counts=(trips, tsum, ntri))["b"]
     assert np.allclose(b1, b2, rtol=1e-12, atol=0)
+
+
+def test_gaussian_scatter_follows_eq_3_3():
+    """For a Gaussian field (B = 0) and three distinct shells every closed triangle is its own
+    term (Wick pairings match only identical triangles), so Var(B_hat) = V sum_T P_a P_b P_c /
+    N_tri^2; Eq. (3.3) at the shells' mean powers gives the same to the spread of P over a
+    shell. Both against the scatter of 400 seeded realisations."""
+    ng, n_index = 32, 2.0
+    pl = P.make_plan(ng, float(ng), P.linear_edges(8, 1.0, 8.0))
+    trips, tsum, ntri = fbe.kept_triplets(pl)
+    sel = [i for i, (a, b, c) in enumerate(trips) if a > b > c]
+    m = np.fft.fftfreq(ng, 1.0 / ng)
+    mz = np.arange(ng // 2 + 1, dtype=np.float64)
+    q = m[:, None, None] ** 2 + m[None, :, None] ** 2 + mz[None, None, :] ** 2
+    pk = np.where(q > 0, (pl.kf * np.sqrt(np.where(q > 0, q, 1.0))) ** (-n_index), 0.0)
+    pf = fbe.shell_fields(pk, pl)
+    sum_ppp = fbe.triple_sums(pf, [trips[i] for i in sel]) / float(ng) ** 3
+    n = ntri[sel].astype(float)
+    var_exact = pl.volume * sum_ppp / n ** 2
+    counts = (trips, tsum, ntri)
+    bs = np.array([fbe.estimate(fieldgen.spectrum(fieldgen.gaussian_field(ng, float(ng), n_index, 700 + s)),
+                                pl, counts=counts)["b"][sel] for s in range(400)])
+    ratio = bs.var(0, ddof=1) / var_exact
+    assert 0.85 < np.median(ratio) < 1.15
+    assert np.all((ratio > 0.6) & (ratio < 1.6))
+    # Eq. (3.3) with B = 0 at the mean power of each shell's modes
+    sidx = P.shell_index_half(pl)
+    full = np.ones_like(q)
+    full[..., 1:ng // 2] = 2.0                       # half-grid modes stand for two of the full grid
+    pbar = np.array([np.sum((pk * full)[sidx == s]) / np.sum(full[sidx == s]) for s in range(pl.ns)])
+    a, b, c = (np.array([trips[i][j] for i in sel]) for j in range(3))
+    sig = A.sigma_b(pbar[a], pbar[b], pbar[c], 0.0, n, pl.volume)
+    # the shell-mean form is an approximation where P changes fast across a shell (k^-2 on the
+    # innermost shells, whose width is comparable to their radius)
+    dev = np.abs(sig ** 2 / var_exact - 1.0)
+    assert np.median(dev) < 0.05 and np.max(dev) < 0.5
