@@ -66,10 +66,10 @@ bsp_status run_contract(bsp_plan* p, const void* fields, double* msum, cudaStrea
     if (p->prec == BSP_MIXED_BF16X3) {
       TcArgs a{};
       a.nvox = L.nvox();
-      a.ns = (int)L.shells.size();
       a.np = L.np;
-      a.pair_ab = L.d_tc_pairs;
-      a.n_mtiles = L.mtiles;
+      a.kt = L.kt;
+      a.groups = L.d_tc_groups;
+      a.n_tg = L.n_tg;
       a.gridy = L.gridy;
       a.vox_per_block = L.vpb;
       a.partial = L.tc_partial;
@@ -116,7 +116,7 @@ bsp_status run_contract(bsp_plan* p, const void* fields, double* msum, cudaStrea
 int contract_launches(const bsp_plan* p) {
   int n = 0;
   for (const ContractLevel& L : p->levels) {
-    const bool work = p->prec == BSP_MIXED_BF16X3 ? L.mtiles > 0 : L.ntiles > 0;
+    const bool work = p->prec == BSP_MIXED_BF16X3 ? L.n_tg > 0 : L.ntiles > 0;
     const bool sampled = !L.top && !(p->prec == BSP_MIXED_BF16X3 && p->n_zlev > 0);  // else the Z pass did it
     n += sampled + (p->prec == BSP_MIXED_BF16X3 ? 1 : 2) * work;
   }

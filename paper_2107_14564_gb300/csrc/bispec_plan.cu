@@ -113,43 +113,204 @@ void make_tiles(const std::vector<int>& ta, const std::vector<int>& tb, const st
   }
 }
 
-// Rows of the tensor-core contraction: pair i goes to row row_of[i]. Every row costs the same
-// generation work, so pairs are packed densely; their order only matters for shared-memory bank
-// conflicts. A generator thread reads 16 bytes of field a and of field b of its row per load, and
-// a 128-bit load is served in four phases of 8 consecutive lanes; field n's 16 bytes sit in bank
-// group n mod 8 of their 128-byte line (the TMA's swizzle), so a phase is conflict-free when its
-// distinct a take distinct values mod 8, and its distinct b too. Rows are filled 8 at a time by
-// first fit over the pairs in (a, b) order. Padding rows of a phase repeat its first pair, encoded
-// as (-a - 1, -b - 1) (a broadcast, never read back). Returns the number of rows (multiple of 8).
-int assign_tc_rows(const std::vector<int2>& pairs, std::vector<int>& row_of, std::vector<int2>& rows) {
-  row_of.assign(pairs.size(), -1);
-  rows.clear();
-  std::vector<int> pending(pairs.size());
-  for (size_t i = 0; i < pairs.size(); ++i) pending[i] = (int)i;
-  while (!pending.empty()) {
-    int a_at[8], b_at[8];
-    for (int k = 0; k < 8; ++k) a_at[k] = b_at[k] = -1;
-    std::vector<int> take, rest;
-    for (int i : pending) {
-      const int a = pairs[i].x, b = pairs[i].y;
-      const bool fit = take.size() < 8 && (a_at[a & 7] < 0 || a_at[a & 7] == a) && (b_at[b & 7] < 0 || b_at[b & 7] == b);
-      if (fit) {
-        a_at[a & 7] = a;
-        b_at[b & 7] = b;
-        take.push_back(i);
-      } else {
-        rest.push_back(i);
-      }
-    }
-    for (int i : take) {
-      row_of[i] = (int)rows.size();
-      rows.push_back(pairs[i]);
-    }
-    const int2 first = pairs[take[0]];
-    while (rows.size() % 8 != 0) rows.push_back(make_int2(-first.x - 1, -first.y - 1));
-    pending.swap(rest);
+// Pair groups of the tensor-core contraction (see TcArgs). A slot holds three fields f0, f1, f2
+// and the flag s; its pairs are (f0, s ? f1 : f0) in tile 0, (f0, f2) in tile 1 and (f1, f2) in
+// tile 2 of its tile group, so one generator thread forms KT pair products from three loaded
+// fields. Every tile of a tile group costs the same MMAs, so the grouping minimises tiles (tile
+// groups x KT) and, at equal cost, takes the larger KT (fewer field loads per pair).
+//
+// Groups are chosen greedily and deterministically: the uncovered pair whose best candidate group
+// covers the fewest uncovered pairs (then: has the fewest such candidates) is covered next, by
+// its candidate that covers the most uncovered pairs and, among those, leaves the easiest pairs
+// for later (lowest sum of their best scores).
+namespace {
+struct Grp {
+  int f0, f1, f2, s;
+};
+void grp_pairs(const Grp& g, int2 out[3]) {
+  out[0] = make_int2(g.f0, g.s ? g.f1 : g.f0);
+  out[1] = make_int2(g.f0, g.f2);
+  out[2] = make_int2(g.f1, g.f2);
+}
+}  // namespace
+
+TcGrouping group_pairs(const std::vector<int2>& pairs, int nf, int kt_max) {
+  const int np = (int)pairs.size();
+  std::vector<int> id((size_t)nf * nf, -1);
+  for (int i = 0; i < np; ++i) {
+    id[(size_t)pairs[i].x * nf + pairs[i].y] = i;
+    id[(size_t)pairs[i].y * nf + pairs[i].x] = i;
   }
-  return (int)rows.size();
+  auto pid = [&](int2 q) { return id[(size_t)q.x * nf + q.y]; };
+  // greedy cover with groups of kt pairs
+  auto cover = [&](int kt) {
+    std::vector<Grp> groups;
+    std::vector<char> unc(np, 1);
+    int left = np;
+    // distinct uncovered pairs a group covers in its first kt tiles
+    auto score = [&](const Grp& g) {
+      int2 q[3];
+      grp_pairs(g, q);
+      int ids[3], n = 0;
+      for (int j = 0; j < kt; ++j) {
+        const int k = pid(q[j]);
+        if (k < 0 || !unc[k]) continue;
+        bool dup = false;
+        for (int t = 0; t < n; ++t) dup |= ids[t] == k;
+        if (!dup) ids[n++] = k;
+      }
+      return n;
+    };
+    auto cands = [&](int i, std::vector<Grp>& out) {
+      out.clear();
+      const int a = pairs[i].x, b = pairs[i].y;
+      const int xs[2][2] = {{a, b}, {b, a}};
+      for (int o = 0; o < (a == b ? 1 : 2); ++o) {
+        const int x = xs[o][0], y = xs[o][1];
+        for (int f = 0; f < nf; ++f) out.push_back({x, y, f, 1});  // tile 0 (f0, f1)
+        for (int f = 0; f < nf; ++f) {                              // tile 1 (f0, f2)
+          out.push_back({x, f, y, 1});
+          if (kt >= 3 || f == 0) out.push_back({x, kt >= 3 ? f : x, y, 0});  // f1 unused at kt 2
+        }
+        if (kt >= 3)
+          for (int f = 0; f < nf; ++f)                              // tile 2 (f1, f2)
+            for (int s = 0; s < 2; ++s) out.push_back({f, x, y, s});
+      }
+      if (a == b) {                                                 // tile 0 (f0, f0)
+        for (int f2 = 0; f2 < nf; ++f2)
+          for (int f1 = 0; f1 < (kt >= 3 ? nf : 1); ++f1) out.push_back({a, kt >= 3 ? f1 : a, f2, 0});
+      }
+    };
+    std::vector<Grp> cs;
+    std::vector<int> best(np, 0);
+    while (left > 0) {
+      int pick = -1, pick_m = 0, pick_cnt = 0;
+      for (int i = 0; i < np; ++i) {
+        if (!unc[i]) continue;
+        cands(i, cs);
+        int m = 0, cnt = 0;
+        for (const Grp& g : cs) {
+          const int sc = score(g);
+          if (sc > m) { m = sc; cnt = 1; } else if (sc == m) { ++cnt; }
+        }
+        best[i] = m;
+        if (pick < 0 || m < pick_m || (m == pick_m && cnt < pick_cnt)) { pick = i; pick_m = m; pick_cnt = cnt; }
+      }
+      cands(pick, cs);
+      Grp chosen = cs[0];
+      long long chosen_h = -1;
+      for (const Grp& g : cs) {
+        if (score(g) != pick_m) continue;
+        int2 q[3];
+        grp_pairs(g, q);
+        long long h = 0;
+        for (int j = 0; j < kt; ++j) {
+          const int k = pid(q[j]);
+          if (k >= 0 && unc[k]) h += best[k];
+        }
+        if (chosen_h < 0 || h < chosen_h) { chosen = g; chosen_h = h; }
+      }
+      int2 q[3];
+      grp_pairs(chosen, q);
+      for (int j = 0; j < kt; ++j) {
+        const int k = pid(q[j]);
+        if (k >= 0 && unc[k]) { unc[k] = 0; --left; }
+      }
+      groups.push_back(chosen);
+    }
+    return groups;
+  };
+  // candidate groupings: one pair per slot, or greedy groups of 2 and 3
+  std::vector<Grp> best_groups;
+  int best_kt = 1;
+  for (int i = 0; i < np; ++i) best_groups.push_back({pairs[i].x, pairs[i].y, pairs[i].x, 1});
+  long long best_cost = (np + kTcSlots - 1) / kTcSlots;
+  if (np > kTcSlots) {
+    for (int kt = 2; kt <= kt_max; ++kt) {
+      std::vector<Grp> g = cover(kt);
+      const long long cost = (long long)kt * (((long long)g.size() + kTcSlots - 1) / kTcSlots);
+      if (cost <= best_cost) { best_cost = cost; best_kt = kt; best_groups.swap(g); }
+    }
+  }
+  // Slot order: a generator's 8-byte shared-memory load of field slot f is served in half-warp
+  // phases of 4 consecutive slots, each slot's quad reading the 32-byte segment (K ^ (n >> 1)) & 3
+  // of field n's swizzled 128-byte row (K the K step). A phase is conflict-free when, for every
+  // field slot, its 4 slots read equal fields or fields with distinct (n >> 1) & 3. Phases are
+  // filled greedily, each group in the first of its equivalent field orders that fits (a triangle
+  // may permute its three fields, a group of two its last two, a single pair its two); slots a
+  // phase cannot fill without a conflict take the next group as it is, and padding slots repeat
+  // a group of their phase (a broadcast) with the active flag clear.
+  const int nfld = best_kt == 1 ? 2 : 3;
+  auto orders = [&](const Grp& g, std::vector<Grp>& out) {
+    out.clear();
+    out.push_back(g);
+    if (!g.s) return;
+    if (best_kt == 1) {
+      out.push_back({g.f1, g.f0, g.f1, 1});
+    } else if (best_kt == 2) {
+      out.push_back({g.f0, g.f2, g.f1, 1});
+    } else {
+      const int f[3] = {g.f0, g.f1, g.f2};
+      const int perm[5][3] = {{0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+      for (auto& p : perm) out.push_back({f[p[0]], f[p[1]], f[p[2]], 1});
+    }
+  };
+  auto fld = [](const Grp& g, int f) { return f == 0 ? g.f0 : f == 1 ? g.f1 : g.f2; };
+  std::vector<Grp> placed;  // in slot order; (-1, ...) marks padding
+  {
+    std::vector<Grp> rest = best_groups, ords;
+    while (!rest.empty()) {
+      int used[3][4];
+      for (auto& u : used) for (int& x : u) x = -1;
+      int n = 0;
+      for (size_t k = 0; k < rest.size() && n < 4;) {
+        orders(rest[k], ords);
+        bool put = false;
+        for (const Grp& o : ords) {
+          bool ok = true;
+          for (int f = 0; f < nfld && ok; ++f) {
+            const int v = fld(o, f), b = (v >> 1) & 3;
+            ok = used[f][b] < 0 || used[f][b] == v;
+          }
+          if (!ok) continue;
+          for (int f = 0; f < nfld; ++f) used[f][(fld(o, f) >> 1) & 3] = fld(o, f);
+          placed.push_back(o);
+          put = true;
+          break;
+        }
+        if (put) { rest.erase(rest.begin() + (long)k); ++n; } else { ++k; }
+      }
+      if (n == 0) { placed.push_back(rest.front()); rest.erase(rest.begin()); ++n; }
+      const bool last = rest.empty();
+      // a phase that could not be completed without conflicts takes the next groups as they are
+      while (n < 4 && !rest.empty() && !last) { placed.push_back(rest.front()); rest.erase(rest.begin()); ++n; }
+      while (n < 4) { placed.push_back({-1, 0, 0, 0}); ++n; }
+    }
+  }
+  TcGrouping out;
+  out.kt = best_kt;
+  const int nslots = (int)placed.size();
+  out.n_tg = np == 0 ? 0 : (nslots + kTcSlots - 1) / kTcSlots;
+  out.slots.assign((size_t)out.n_tg * kTcSlots, make_int4(0, 0, 0, 0));
+  out.where.assign(np, -1);
+  for (int g = 0; g < nslots; ++g) {
+    const int ph0 = g - g % 4;
+    if (placed[g].f0 < 0) {  // padding: repeat the phase's first group, inactive
+      const Grp& r = placed[ph0];
+      out.slots[g] = make_int4(r.f0, r.f1, r.f2, r.s ? 1 : 0);
+      continue;
+    }
+    const Grp& gr = placed[g];
+    out.slots[g] = make_int4(gr.f0, gr.f1, gr.f2, (gr.s ? 1 : 0) | 2);
+    int2 q[3];
+    grp_pairs(gr, q);
+    const int tg = g / kTcSlots, slot = g % kTcSlots;
+    for (int j = 0; j < out.kt; ++j) {
+      const int k = pid(q[j]);
+      if (k >= 0 && out.where[k] < 0) out.where[k] = (tg * out.kt + j) * kTcSlots + slot;
+    }
+  }
+  return out;
 }
 
 // Shell fields of one precision: X, Y, Z passes for every shell.
@@ -416,7 +577,7 @@ bsp_status autotune_levels(bsp_plan* p, cudaStream_t s) {
   if (ce != cudaSuccess) { cudaEventDestroy(e0); return cuda_fail(ce, "cudaEventCreate"); }
   bsp_status st = BSP_OK;
   for (ContractLevel& L : p->levels) {
-    if (L.mtiles == 0) continue;
+    if (L.n_tg == 0) continue;
     const long long chunks = L.nvox() / kTcVoxelChunk;
     float best = 1e30f;
     long long best_vpb = L.vpb;
@@ -428,10 +589,10 @@ bsp_status autotune_levels(bsp_plan* p, cudaStream_t s) {
       if (gridy > L.gridy_cap && gridy > L.gridy) continue;
       TcArgs a{};
       a.nvox = L.nvox();
-      a.ns = (int)L.shells.size();
       a.np = L.np;
-      a.pair_ab = L.d_tc_pairs;
-      a.n_mtiles = L.mtiles;
+      a.kt = L.kt;
+      a.groups = L.d_tc_groups;
+      a.n_tg = L.n_tg;
       a.gridy = gridy;
       a.vox_per_block = vpb;
       a.partial = L.tc_partial;
@@ -570,21 +731,15 @@ bsp_status build_levels(bsp_plan* p, cudaStream_t s) {
     void* tmp = nullptr;
     if (p->prec == BSP_MIXED_BF16X3) {
       L.np = tc_padded_shells(nsh);
-      std::vector<int> row_of;
-      std::vector<int2> rows;
-      const int nrows = assign_tc_rows(pairs, row_of, rows);
-      L.mtiles = (nrows + 127) / 128;
-      // 8-row phases dealt round-robin over the M tiles, so every tile has the same work
-      const int mt = std::max(L.mtiles, 1);
-      auto place = [mt](int r) { const int ph = r / 8; return (ph % mt) * 128 + (ph / mt) * 8 + r % 8; };
-      std::vector<int2> pab((size_t)mt * 128, make_int2(-1, -1));
-      for (int i = 0; i < nrows; ++i) pab[place(i)] = rows[i];
-      for (int& r : row_of) r = place(r);
+      const TcGrouping G = group_pairs(pairs, nsh, L.np == 32 ? 3 : 2);
+      L.kt = G.kt;
+      L.n_tg = G.n_tg;
       std::vector<int> tmap(L.bins.size());
       int pi = -1;
       for (size_t i = 0; i < L.bins.size(); ++i) {
         if (i == 0 || la[i] != la[i - 1] || lb[i] != lb[i - 1]) ++pi;
-        tmap[i] = row_of[pi] * L.np + lc[i];
+        if (G.where[pi] < 0) return fail(BSP_ERR_CUDA, "internal: a pair of the contraction has no slot");
+        tmap[i] = G.where[pi] * L.np + lc[i];
       }
       const long long chunks = L.nvox() / kTcVoxelChunk;
       long long gy = std::min<long long>(std::max(1, p->n_sm), chunks);
@@ -593,11 +748,11 @@ bsp_status build_levels(bsp_plan* p, cudaStream_t s) {
       // partial sums sized for the largest split the autotuner may pick
       const long long gmax = p->autotune ? std::min<long long>((long long)kTuneMults[kNumTune - 1] * std::max(1, p->n_sm), chunks) : gy;
       L.gridy_cap = (int)((L.nvox() + ((chunks + gmax - 1) / gmax) * kTcVoxelChunk - 1) / (((chunks + gmax - 1) / gmax) * kTcVoxelChunk));
-      if ((st = dev_upload(p, pab, &L.d_tc_pairs, s)) != BSP_OK) return st;
+      if ((st = dev_upload(p, G.slots, &L.d_tc_groups, s)) != BSP_OK) return st;
       L.tc_off = tmap;
-      if ((st = dev_alloc(p, tc_partial_doubles(std::max(L.mtiles, 1), std::max(L.gridy, L.gridy_cap), L.np) * sizeof(double), &tmp)) != BSP_OK)
+      if ((st = dev_alloc(p, tc_partial_entries(std::max(L.n_tg, 1), std::max(L.kt, 1), std::max(L.gridy, L.gridy_cap), L.np) * sizeof(float2), &tmp)) != BSP_OK)
         return st;
-      L.tc_partial = static_cast<double*>(tmp);
+      L.tc_partial = static_cast<float2*>(tmp);
     } else {
       L.ntiles = (int)tiles.size();
       L.gridx = pick_gridx_n(p->n_sm, L.ntiles, L.nvox());
@@ -615,7 +770,7 @@ bsp_status build_levels(bsp_plan* p, cudaStream_t s) {
       if ((st = dev_upload(p, src, &L.d_shells, s)) != BSP_OK) return st;
       if ((st = dev_alloc(p, (size_t)nsh * (size_t)L.nvox() * re, &L.fields)) != BSP_OK) return st;
     }
-    if (p->prec == BSP_MIXED_BF16X3 && L.mtiles > 0) {
+    if (p->prec == BSP_MIXED_BF16X3 && L.n_tg > 0) {
       st = encode_split_map(&L.tmap, L.top ? p->fields : L.fields, L.nvox(), nsh, L.np);
       if (st != BSP_OK) return st;
     }
@@ -643,7 +798,7 @@ bsp_status build_levels(bsp_plan* p, cudaStream_t s) {
       for (size_t i = 0; i < L.bins.size(); ++i) {
         TcBin& b = tb[L.bins[i]];
         b.partial = L.tc_partial;
-        b.stride = (long long)L.mtiles * 128 * L.np;
+        b.stride = (long long)L.n_tg * L.kt * kTcSlots * L.np;
         b.gridy = L.gridy;
         b.off = L.tc_off[i];
         b.scale = L.scale;

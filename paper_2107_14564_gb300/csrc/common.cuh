@@ -188,23 +188,28 @@ struct FinalizeArgs {
 bsp_status launch_finalize(const FinalizeArgs& a, cudaStream_t s);
 
 // ---------------------------------------------------------------- tensor-core contraction
-constexpr int kTcVoxelChunk = 128;  // voxels per pipeline stage of the tensor-core contraction
+constexpr int kTcVoxelChunk = 64;  // voxels per pipeline stage of the tensor-core contraction
+constexpr int kTcSlots = 64;       // pair-group slots of one tile group (a 128-lane M tile of hi/lo rows)
 // Split fields: d = d_hi + d_lo with d_hi = bf16(d) and d_lo = bf16(d - d_hi), stored as two
 // bf16 planes [2][ns][nvox] (high parts first). The contraction reads them through a 3D tensor
 // map (voxel, shell, part) with 64 x NP x 1 boxes and the 128-byte swizzle.
+//
+// Pairs are packed into groups of up to KT pairs built from three fields (f0, f1, f2) of one
+// slot: tile 0 holds the pair (f0, s ? f1 : f0), tile 1 (f0, f2), tile 2 (f1, f2), where s is
+// bit 0 of the slot's flags; bit 1 marks a slot holding at least one kept pair.
 struct TcArgs {
   long long nvox;           // multiple of kTcVoxelChunk
-  int ns;
   int np;                   // shells padded for the MMA N dimension (32 or 64)
-  const int2* pair_ab;      // [n_mtiles * 128] (a, b), (-1, -1) on padding rows
-  int n_mtiles;
+  int kt;                   // pair tiles per tile group (1..3; 1..2 when np = 64)
+  const int4* groups;       // [n_tg * kTcSlots] (f0, f1, f2, flags)
+  int n_tg;                 // tile groups
   int gridy;                // voxel blocks
   long long vox_per_block;  // multiple of kTcVoxelChunk
-  double* partial;          // [gridy][n_mtiles][128][np]
+  float2* partial;          // [gridy][n_tg][kt][kTcSlots][np] run sums as FP32 pairs s + c
   int* error;               // set to 1 when a bounded wait gives up
 };
 int tc_padded_shells(int ns);
-size_t tc_partial_doubles(int n_mtiles, int gridy, int np);
+size_t tc_partial_entries(int n_tg, int kt, int gridy, int np);
 bsp_status launch_contract_tc(const TcArgs& a, const CUtensorMap* tmap, cudaStream_t s);
 // Encode the tensor map of split fields at `base` ([2][rows][nvox] bf16) for NP-row boxes.
 bsp_status encode_split_map(CUtensorMap* map, void* base, long long nvox, int rows, int np);
@@ -212,7 +217,7 @@ bsp_status encode_split_map(CUtensorMap* map, void* base, long long nvox, int ro
 bsp_status launch_split_fields(const float* src, uint32_t* dst, long long n_words, int n_sm, cudaStream_t s);
 // One kept bin of the tensor-core contraction: msum[t] = scale * sum_y partial[y * stride + off].
 struct TcBin {
-  const double* partial;
+  const float2* partial;
   long long stride;
   int gridy;
   int off;

@@ -61,13 +61,13 @@ struct ContractLevel {
   int ntiles = 0, gridx = 0;
   double* partial = nullptr;
   // tensor-core contraction
-  int np = 0, mtiles = 0, gridy = 0;
+  int np = 0, kt = 0, n_tg = 0, gridy = 0;  // padded shells, pair tiles per tile group, tile groups
   long long vpb = 0;
-  int2* d_tc_pairs = nullptr;
+  int4* d_tc_groups = nullptr;  // [n_tg * kTcSlots] slot fields and flags (see TcArgs)
   std::vector<int> tc_off;    // partial-sum entry of each of the level's bins
   int gridy_cap = 0;          // voxel blocks the partial-sum buffer holds
   int tune_mult = 1;          // blocks per M tile / SM count chosen by the autotuner (1 without it)
-  double* tc_partial = nullptr;
+  float2* tc_partial = nullptr;
   int dim = 3;                // 2: a level of a 2D plan (g^2 points)
   long long nvox() const { return dim == 2 ? (long long)g * g : (long long)g * g * g; }
 };
@@ -202,6 +202,15 @@ void make_tiles(const std::vector<int>& ta, const std::vector<int>& tb, const st
                 std::vector<int2>& pairs, std::vector<Tile>& tiles, std::vector<int>& map,
                 const std::vector<int>* ids = nullptr);
 int pick_gridx_n(int n_sm, int ntiles, long long nvox);
+// Pair groups of the tensor-core contraction of one level: the slots (f0, f1, f2, flags) of n_tg
+// tile groups of kt tiles, and where[i] = (tg * kt + j) * kTcSlots + slot for pair i.
+struct TcGrouping {
+  int kt = 1;
+  int n_tg = 0;
+  std::vector<int4> slots;
+  std::vector<int> where;
+};
+TcGrouping group_pairs(const std::vector<int2>& pairs, int nf, int kt_max);
 long long g1_elems(const bsp_plan* p);
 long long g2_elems(const bsp_plan* p);
 
