@@ -66,6 +66,42 @@ def test_closed_form_three_cosines():
     assert max(others) <= 1e-9 * float(ng) ** 12
 
 
+def test_kaiser_factor_special_modes():
+    """Eq. (3.4) at modes whose angle to the line of sight (z) is known by construction: along z
+    the factor is 1 + beta, across it 1, at 45 degrees in the x-z plane 1 + beta/2, and on the
+    3-4-5 direction (4, 0, 3) it is 1 + 9 beta/25; k = 0 keeps factor 1."""
+    ng, beta = 16, 0.7
+    f = fbe.kaiser_factor_half(ng, beta)
+    assert f[0, 0, 0] == 1.0
+    assert abs(f[0, 0, 5] - (1 + beta)) < 1e-15
+    assert abs(f[5, 0, 0] - 1.0) < 1e-15 and abs(f[0, 5, 0] - 1.0) < 1e-15
+    assert abs(f[3, 0, 3] - (1 + beta / 2)) < 1e-15 and abs(f[ng - 3, 0, 3] - (1 + beta / 2)) < 1e-15
+    assert abs(f[4, 0, 3] - (1 + 9 * beta / 25)) < 1e-15 and abs(f[0, ng - 4, 3] - (1 + 9 * beta / 25)) < 1e-15
+
+
+def test_closed_form_three_cosines_with_rsd():
+    """Three plane waves of amplitude 2A on a 3-4-5 triangle, m1 = (0, 0, 3) along the line of
+    sight, m2 = (4, 0, -3), m3 = (-4, 0, 0) across it: linear RSD (Eq. (3.4)) multiplies each wave
+    by 1 + beta mu^2 with mu^2 = 1, 9/25 and 0 (the cosines of the triangle's angles with z), so
+    the bin's triple sum is the real-space closed form 2 A^3 Ng^12 times (1 + beta)(1 + 9 beta/25).
+    Using mu for mu^2, the x axis for z, or |m| for |m|^2 changes the product."""
+    ng, amp, beta = 32, 0.7, 0.6
+    pl = _plan(ng)
+    m1, m2 = np.array([0, 0, 3]), np.array([4, 0, -3])
+    m3 = -(m1 + m2)
+    x = np.indices((ng, ng, ng)).reshape(3, -1).T
+    delta = sum(2 * amp * np.cos(2 * np.pi * (x @ m) / ng) for m in (m1, m2, m3)).reshape(ng, ng, ng)
+    sh = [int(np.searchsorted(pl.thresholds, (m * m).sum(), side="right") - 1) for m in (m1, m2, m3)]
+    a, b, c = sorted(sh, reverse=True)
+    assert a > b > c
+    res = fbe.estimate(fieldgen.spectrum(delta), pl, beta=beta)
+    i = res["triplets"].index((a, b, c))
+    want = 2 * amp ** 3 * float(ng) ** 12 * (1 + beta) * (1 + 9 * beta / 25)
+    assert abs(res["msum"][i] - want) <= 1e-10 * want
+    others = [abs(v) for j, v in enumerate(res["msum"]) if j != i]
+    assert max(others) <= 1e-9 * float(ng) ** 12
+
+
 def test_invariants():
     """Translation, the cube symmetries, delta -> alpha delta (alpha^3) and delta -> -delta."""
     ng = 16
