@@ -156,6 +156,14 @@ BSP_API bsp_status bsp_plan_info(const bsp_plan* plan, int* n_triplets, int* n_s
 BSP_API bsp_status bsp_plan_tuning(const bsp_plan* plan, int* n_levels, int* level_side, int* blocks_mult,
                                    int max_levels);
 
+/* Where each kept bin is summed (no counterpart in the paper; for tests and profiling): for bin t
+ * < n (the order of bsp_plan_triplets), level[t] = index of its contraction level (as in
+ * bsp_plan_tuning) and slot[t] = for split-BF16 plans the tensor-core tile and pair slot of its
+ * pair, (tile group x tiles per group + tile) x 64 + slot, else -1. Arrays: host, n entries each
+ * (n = the plan's kept bins), may be NULL. Errors: BSP_ERR_INVALID_ARG for a NULL plan or n other
+ * than the number of kept bins. */
+BSP_API bsp_status bsp_plan_bin_levels(const bsp_plan* plan, int n, int* level, int* slot);
+
 /* Side of the plan's evaluation grid, ng_eval <= ng. Every shell mode has |m_i| <= r - 1, so a
  * triple product of shell fields only holds wavevectors with |k_i| <= 3 (r - 1); summed over any
  * grid of side S > 3 (r - 1) it keeps only k = 0, exactly as the ng^3 grid of Eq. (2.7) does (the
@@ -309,8 +317,10 @@ BSP_API bsp_status bsp_plan_slabs(const bsp_plan* plan, int* slab_planes, int* n
  * calls that overlap on the GPU (other streams, other threads) race and give wrong sums.
  * fields, triplets (int, 3 per bin), msum (n_triplets doubles): device pointers, caller-owned.
  * Errors: BSP_ERR_INVALID_ARG for NULL pointers, n_shells outside [1, BSP_NOALLOC_MAX_SHELLS],
- * n_triplets outside [1, BSP_NOALLOC_MAX_TRIPLETS] or n_vox < 1; BSP_ERR_CUDA. Shell indices must
- * be < n_shells (not checked). Accumulates in FP32 over runs of 1024 voxels and in FP64 across. */
+ * n_triplets outside [1, BSP_NOALLOC_MAX_TRIPLETS] or n_vox < 1; BSP_ERR_CUDA. A bin whose shell
+ * indices are not all in [0, n_shells) gets msum = NaN (the kernel checks every index before it
+ * reads, so no memory outside the inputs is touched). Accumulates in FP32 over runs of 1024 voxels
+ * and in FP64 across. */
 BSP_API bsp_status bsp_triple_sums_noalloc(const float* fields, int n_shells, long long n_vox,
                                            const int* triplets, int n_triplets, double* msum,
                                            void* stream);

@@ -83,6 +83,14 @@ def bsp_plan_tuning(handle):
     return [(int(side[i]), int(mult[i])) for i in range(n.value)]
 
 
+def bsp_plan_bin_levels(handle, n: int):
+    """(level index, tensor-core tile x 64 + slot or -1) of each kept bin."""
+    lev = (C.c_int * max(n, 1))()
+    slot = (C.c_int * max(n, 1))()
+    check(_lib.load().bsp_plan_bin_levels(handle, n, lev, slot))
+    return np.array(lev[:n], dtype=np.int64), np.array(slot[:n], dtype=np.int64)
+
+
 def bsp_plan_triplets(handle) -> np.ndarray:
     tab = C.POINTER(Triplet)()
     n = C.c_int()
@@ -242,6 +250,7 @@ class Plan:
         self.triplets = bsp_plan_triplets(self.handle)
         self.ng_eval = bsp_plan_grid(self.handle)
         self.tuning = bsp_plan_tuning(self.handle)
+        self.bin_level, self.bin_slot = bsp_plan_bin_levels(self.handle, self.n_triplets)
         self.host_input_bytes = bsp_plan_host_input_bytes(self.handle)
         self.slabs = bsp_plan_slabs(self.handle)
         self.pass_tuning = bsp_plan_pass_tuning(self.handle)
@@ -323,5 +332,5 @@ class Plan:
 
 
 __all__ = ["Plan", "BispecError", "bsp_plan_create", "bsp_plan_destroy", "bsp_plan_info",
-           "bsp_plan_triplets", "bsp_plan_grid", "bsp_plan_tuning", "bsp_plan_host_input_bytes", "bsp_plan_slabs", "bsp_plan_pass_tuning", "bsp_shell_fields", "bsp_contract", "bsp_estimate",
+           "bsp_plan_triplets", "bsp_plan_grid", "bsp_plan_tuning", "bsp_plan_bin_levels", "bsp_plan_host_input_bytes", "bsp_plan_slabs", "bsp_plan_pass_tuning", "bsp_shell_fields", "bsp_contract", "bsp_estimate",
            "bsp_estimate_host", "bsp_estimate_batched", "Batch", "bsp_spectrum", "bsp_grad", "bsp_last_sums", "bsp_plan_check", "bsp_version", "TRIPLET_DTYPE"]

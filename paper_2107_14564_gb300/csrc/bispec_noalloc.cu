@@ -37,13 +37,20 @@ noalloc_contract_kernel(const float* __restrict__ fields, int ns, long long nvox
   int ia[kNaPerThread], ib[kNaPerThread], ic[kNaPerThread];
   float acc[kNaPerThread];
   double acc64[kNaPerThread];
+  unsigned bad = 0;  // bit k: bin k of this thread names a shell outside [0, ns)
 #pragma unroll
   for (int k = 0; k < kNaPerThread; ++k) {
     const int t = threadIdx.x + k * kNaThreads;
     const bool ok = t < n_trip;
-    ia[k] = ok ? trip[3 * t + 0] : 0;
-    ib[k] = ok ? trip[3 * t + 1] : 0;
-    ic[k] = ok ? trip[3 * t + 2] : 0;
+    const int a = ok ? trip[3 * t + 0] : 0;
+    const int b = ok ? trip[3 * t + 1] : 0;
+    const int c = ok ? trip[3 * t + 2] : 0;
+    const bool in = a >= 0 && a < ns && b >= 0 && b < ns && c >= 0 && c < ns;
+    // a bin with a shell index outside the fields reads shell 0 instead and reports NaN
+    ia[k] = in ? a : 0;
+    ib[k] = in ? b : 0;
+    ic[k] = in ? c : 0;
+    bad |= in ? 0u : 1u << k;
     acc[k] = 0.f;
     acc64[k] = 0.0;
   }
@@ -73,7 +80,9 @@ noalloc_contract_kernel(const float* __restrict__ fields, int ns, long long nvox
 #pragma unroll
   for (int k = 0; k < kNaPerThread; ++k) {
     const int t = threadIdx.x + k * kNaThreads;
-    if (t < n_trip) partial[(long long)blockIdx.x * n_trip + t] = acc64[k] + (double)acc[k];
+    if (t < n_trip)
+      partial[(long long)blockIdx.x * n_trip + t] = (bad >> k) & 1u ? __longlong_as_double(0x7ff8000000000000LL)
+                                                                      : acc64[k] + (double)acc[k];
   }
 }
 

@@ -1135,6 +1135,19 @@ bsp_status bsp_plan_tuning(const bsp_plan* p, int* n_levels, int* level_side, in
   return BSP_OK;
 }
 
+bsp_status bsp_plan_bin_levels(const bsp_plan* p, int n, int* level, int* slot) {
+  if (!p) return fail(BSP_ERR_INVALID_ARG, "NULL argument");
+  if (n != (int)p->trips.size()) return fail(BSP_ERR_INVALID_ARG, "n must be the number of kept bins");
+  for (int l = 0; l < (int)p->levels.size(); ++l) {
+    const ContractLevel& L = p->levels[l];
+    for (size_t i = 0; i < L.bins.size(); ++i) {
+      if (level) level[L.bins[i]] = l;
+      if (slot) slot[L.bins[i]] = p->prec == BSP_MIXED_BF16X3 && L.np > 0 ? L.tc_off[i] / L.np : -1;
+    }
+  }
+  return BSP_OK;
+}
+
 bsp_status bsp_plan_grid(const bsp_plan* p, int* ng_eval) {
   if (!p || !ng_eval) return fail(BSP_ERR_INVALID_ARG, "NULL argument");
   *ng_eval = p->ngs;
