@@ -256,7 +256,9 @@ BSP_API bsp_status bsp_batch_destroy(bsp_batch* batch);
 BSP_API bsp_status bsp_last_sums(const bsp_plan* plan, const double** msum);
 
 /* Synchronise `stream` and report a device-side failure raised by an earlier call on this plan:
- * BSP_ERR_TIMEOUT if a bounded wait inside a kernel gave up (the call's results are invalid). */
+ * BSP_ERR_TIMEOUT if a bounded wait inside a kernel gave up (the call's results are invalid). The
+ * plan's failure flag is cleared when it is reported, so a later check reports only failures of
+ * calls made after this one. */
 BSP_API bsp_status bsp_plan_check(bsp_plan* plan, void* stream);
 
 /* Stages of one bsp_estimate, in launch order (for bsp_timing_read and bsp_plan_stage_work). */

@@ -501,7 +501,11 @@ bsp_status bsp_plan_check(bsp_plan* p, void* stream) {
   BSP_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
   int flag = 0;
   BSP_CUDA(cudaMemcpy(&flag, p->d_error, sizeof(int), cudaMemcpyDeviceToHost));
-  if (flag) return fail(BSP_ERR_TIMEOUT, "a bounded device-side wait gave up in an earlier call");
+  if (flag) {
+    // reported once: later checks report only later give-ups
+    BSP_CUDA(cudaMemset(p->d_error, 0, sizeof(int)));
+    return fail(BSP_ERR_TIMEOUT, "a bounded device-side wait gave up in an earlier call");
+  }
   return BSP_OK;
 }
 
