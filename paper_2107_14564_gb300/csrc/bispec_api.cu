@@ -127,8 +127,30 @@ int contract_launches(const bsp_plan* p) {
 // fields in p->fields, its sums added to msum after the first slab.
 template <typename T>
 bsp_status contract_slab(bsp_plan* p, int k, cudaStream_t s) {
-  if (p->levels.empty() || p->levels[0].ntiles == 0) return BSP_OK;
+  if (p->levels.empty()) return BSP_OK;
   const ContractLevel& L = p->levels[0];
+  if (p->prec == BSP_MIXED_BF16X3) {
+    // the slab's split fields through the full-slab or last-slab tensor map, a fixed number of
+    // voxel blocks (blocks past the slab's voxels write zero sums), sums added over the slabs
+    if (L.n_tg == 0) return BSP_OK;
+    const long long nvox = (long long)p->slab_len(k) * p->ngs * p->ngs;
+    const long long chunks = nvox / kTcVoxelChunk;
+    TcArgs a{};
+    a.nvox = nvox;
+    a.np = L.np;
+    a.kt = L.kt;
+    a.groups = L.d_tc_groups;
+    a.n_tg = L.n_tg;
+    a.gridy = L.gridy;
+    a.vox_per_block = ((chunks + L.gridy - 1) / L.gridy) * kTcVoxelChunk;
+    a.partial = L.tc_partial;
+    a.error = p->d_error;
+    const bool last = k == p->n_slabs() - 1 && p->slab_len(k) != p->slab_len(0);
+    bsp_status st = launch_contract_tc(a, last ? &L.tmap_last : &L.tmap, s);
+    if (st != BSP_OK) return st;
+    return launch_reduce_tc_all(p->d_tc_bins, (int)p->trips.size(), p->msum, s, k > 0);
+  }
+  if (L.ntiles == 0) return BSP_OK;
   ContractArgs c{};
   c.fields = p->fields;
   c.nvox = (long long)p->slab_len(k) * p->ngs * p->ngs;
@@ -195,6 +217,8 @@ bsp_status plan_passes(bsp_plan* p, const void* spec, void* fields, cudaStream_t
       a.slab_x0 = p->slab_x0(part);
       a.slab_nx = p->slab_len(part);
       lines = (long long)p->ns * a.slab_nx * p->ngs;
+      // split fields of the slab: [2][ns][slab planes x S^2]
+      if (split) a.split_lo = (long long)p->ns * a.slab_nx * p->ngs * p->ngs / 2;
     }
     st = launch_warp_zpass(a, lines, p->n_sm, s);
     if (st != BSP_OK) return st;
@@ -261,10 +285,10 @@ bsp_status estimate_impl(bsp_plan* p, const void* spec, double* b_trip, double* 
   if (p->slab_nx) {
     // memory budget: X and Y passes once, then the Z pass and the contraction slab by slab (the
     // timing's Z-pass stage covers all slabs' Z passes and contractions)
-    st = plan_passes<T>(p, spec, p->fields, s, rec ? ev + 1 : nullptr, false, kPassXY);
+    st = plan_passes<T>(p, spec, p->fields, s, rec ? ev + 1 : nullptr, split, kPassXY);
     if (st != BSP_OK) return st;
     for (int k = 0; k < p->n_slabs(); ++k) {
-      if ((st = plan_passes<T>(p, spec, p->fields, s, nullptr, false, k)) != BSP_OK) return st;
+      if ((st = plan_passes<T>(p, spec, p->fields, s, nullptr, split, k)) != BSP_OK) return st;
       if ((st = contract_slab<T>(p, k, s)) != BSP_OK) return st;
     }
     if (rec) {
@@ -302,7 +326,7 @@ bsp_status estimate_impl(bsp_plan* p, const void* spec, double* b_trip, double* 
       int passes = p->warp_fft ? 2 + p->n_slabs() : (p->nxi > 0) + (p->nyi > 0);
       if (!p->warp_fft)
         for (int k = 0; k < p->n_slabs(); ++k) passes += p->zi_off[k + 1] > p->zi_off[k];
-      const bool work = !p->levels.empty() && p->levels[0].ntiles > 0;
+      const bool work = !p->levels.empty() && (split ? p->levels[0].n_tg > 0 : p->levels[0].ntiles > 0);
       p->launches += passes + 2LL * work * p->n_slabs() + 1;
     } else {
       const int passes = (p->warp_fft ? 3 : (p->nxi > 0) + (p->nyi > 0) + (p->nzi > 0) + (split ? 1 : 0)) +
@@ -487,6 +511,8 @@ bsp_status bsp_contract(bsp_plan* p, const void* fields, double* msum, void* str
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (p->prec == BSP_FP64) return run_contract<double>(p, fields, msum, s, nullptr);
   if (p->prec == BSP_MIXED_BF16X3) {
+    if (p->slab_nx)
+      return fail(BSP_ERR_NOT_SUPPORTED, "bsp_contract: a split-BF16 plan under a memory budget holds one x-slab of fields");
     // the tensor-core contraction reads split fields from the plan's buffer
     const bsp_status st = launch_split_fields(static_cast<const float*>(fields), static_cast<uint32_t*>(p->fields),
                                               (long long)p->ns * p->nvox() / 2, p->n_sm, s);

@@ -362,6 +362,19 @@ __global__ void __launch_bounds__(tc_threads<KT>(), 1)
       }
     }
     if (failed) ptx::tmem_st_wait();
+    if (nchunks == 0 && active) {
+      // a block without voxels (a short x-slab of a budgeted plan) still owns its partial sums
+#pragma unroll
+      for (int m = 0; m < kMine; ++m) {
+        const int j = kg + 2 * m;
+        if (j >= KT) break;
+        float2* out = a.partial + ((((size_t)blockIdx.y * a.n_tg + tg) * KT + j) * kTcSlots + slot) * NP;
+#pragma unroll
+        for (int k = 0; k < NP / 8; ++k)
+#pragma unroll
+          for (int e = 0; e < 2; ++e) out[8 * k + 2 * t4 + e] = make_float2(0.f, 0.f);
+      }
+    }
   }
   if (failed) {
     *abort_flag = 1;
@@ -390,7 +403,7 @@ __global__ void split_fields_kernel(const float2* __restrict__ src, uint32_t* __
 
 // msum[t] for the bins of all levels: lane l adds blocks y = l, l + 32, ... in order, then the
 // warp adds its 32 partial sums by a fixed butterfly, so the result does not depend on timing.
-__global__ void reduce_tc_all_kernel(const TcBin* __restrict__ bins, int n, double* __restrict__ msum) {
+__global__ void reduce_tc_all_kernel(const TcBin* __restrict__ bins, int n, double* __restrict__ msum, int accumulate) {
   const int t = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (t >= n) return;
@@ -402,15 +415,15 @@ __global__ void reduce_tc_all_kernel(const TcBin* __restrict__ bins, int n, doub
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) msum[t] = b.scale * s;
+  if (lane == 0) msum[t] = accumulate ? msum[t] + b.scale * s : b.scale * s;
 }
 
 }  // namespace
 
-bsp_status launch_reduce_tc_all(const TcBin* bins, int n, double* msum, cudaStream_t s) {
+bsp_status launch_reduce_tc_all(const TcBin* bins, int n, double* msum, cudaStream_t s, bool accumulate) {
   if (n == 0) return BSP_OK;
   const long long threads = 32LL * n;
-  reduce_tc_all_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(bins, n, msum);
+  reduce_tc_all_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(bins, n, msum, accumulate ? 1 : 0);
   BSP_CUDA(cudaGetLastError());
   return BSP_OK;
 }

@@ -290,7 +290,8 @@ __global__ void __launch_bounds__(XY<N>::kThreads, XPASS ? 4 : 3) xy_warp_kernel
 }
 
 // ---------------------------------------------------------------- Z pass
-// SLAB: only the x-slab of a.slab_x0 / a.slab_nx, FP32 fields [n][x - slab_x0][y][z].
+// SLAB: only the x-slab of a.slab_x0 / a.slab_nx, fields [n][x - slab_x0][y][z] (FP32, or split
+// planes when a.split_lo != 0).
 template <int S, bool SLAB>
 __global__ void __launch_bounds__(kZThreads, 4) z_warp_kernel(PassArgs a, long long n_lines) {
   constexpr int M = S / 2;
@@ -344,7 +345,7 @@ __global__ void __launch_bounds__(kZThreads, 4) z_warp_kernel(PassArgs a, long l
       }
     warp_fft_from<M, LPL, 0, 1, false>(v, buf, lane, tw);
     const long long off = (long long)n * S * per + xyl * S;  // first voxel of the line
-    if (SLAB || a.split_lo == 0) {
+    if (a.split_lo == 0) {
       float2* dst = reinterpret_cast<float2*>(static_cast<float*>(a.fields) + off);
 #pragma unroll
       for (int b = 0; b < BPLL; ++b)
@@ -366,7 +367,8 @@ __global__ void __launch_bounds__(kZThreads, 4) z_warp_kernel(PassArgs a, long l
           hi[a.split_lo + k] = l;
         }
       // coarser levels: lines with x and y multiples of the level's stride, every t-th voxel
-      if (a.n_zlev > 0) {
+      // (plans streaming x-slabs have one level)
+      if (!SLAB && a.n_zlev > 0) {
         const int x = (int)(xy / S);
         const int y = (int)(xy - (long long)x * S);
         uint32_t mask = zmask[x] & zmask[y];
@@ -622,7 +624,6 @@ bsp_status launch_z(const PassArgs& a, long long n_lines, int n_sm, cudaStream_t
   constexpr int LPW = 32 / Radices<M>::lpl;
   const size_t smem = ((size_t)2 * M + (size_t)(kZThreads / 32) * LPW * pad_len<M>()) * sizeof(float2) +
                       (a.n_zlev > 0 ? (size_t)S * sizeof(uint32_t) : 0);
-  if (a.slab_nx > 0 && a.split_lo != 0) return fail_c(BSP_ERR_NOT_SUPPORTED, "x-slabs of split fields");
   auto kern = a.slab_nx > 0 ? z_warp_kernel<S, true> : z_warp_kernel<S, false>;
   BSP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;

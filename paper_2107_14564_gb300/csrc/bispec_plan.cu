@@ -530,8 +530,9 @@ bsp_status host_plan(bsp_plan* p, const bsp_plan_desc* d) {
   // memory budget: stream x-slabs of the evaluation grid when all fields do not fit
   p->mem_budget = d->mem_budget_bytes;
   if (p->mem_budget > 0 && p->mem_budget < p->field_bytes()) {
-    if (p->prec == BSP_MIXED_BF16X3)
-      return fail(BSP_ERR_NOT_SUPPORTED, "mem_budget_bytes below the shell fields of a split-BF16 plan");
+    if (p->prec == BSP_MIXED_BF16X3 && !(p->dim == 3 && warp_fft_supported(p->ngs)))
+      return fail(BSP_ERR_NOT_SUPPORTED,
+                  "mem_budget_bytes below the shell fields of a split-BF16 plan on an evaluation grid the warp passes do not handle");
     const size_t plane = (size_t)p->ns * p->ngs * p->ngs * p->elem();
     if (p->mem_budget < plane) return fail(BSP_ERR_INVALID_ARG, "mem_budget_bytes below one x-plane of all shell fields");
     p->slab_nx = (int)std::min<size_t>(p->mem_budget / plane, (size_t)p->ngs - 1);
@@ -640,12 +641,15 @@ bsp_status autotune_passes(bsp_plan* p, cudaStream_t s) {
   for (int pass = 0; pass < 2 && st == BSP_OK; ++pass) {
     float best = 1e30f;
     int best_blocks = 0;
+    // a plan streaming x-slabs holds one slab's fields: its Z pass is timed on the first slab
+    const int part = !p->slab_nx ? kPassAll : pass == 0 ? kPassXY : 0;
+    if (p->slab_nx && (st = plan_passes<float>(p, spec, p->fields, s, nullptr, split, kPassXY)) != BSP_OK) break;
     for (int m : mults) {
       *knob[pass] = m * p->n_sm;
       // warm-up (the Y pass needs the X pass output once; the Z pass reads what Y wrote)
-      if ((st = plan_passes<float>(p, spec, p->fields, s, nullptr, split, kPassAll)) != BSP_OK) break;
+      if ((st = plan_passes<float>(p, spec, p->fields, s, nullptr, split, part)) != BSP_OK) break;
       if ((ce = cudaEventRecord(e0, s)) != cudaSuccess) { st = cuda_fail(ce, "cudaEventRecord"); break; }
-      for (int r = 0; r < 3 && st == BSP_OK; ++r) st = plan_passes<float>(p, spec, p->fields, s, nullptr, split, kPassAll);
+      for (int r = 0; r < 3 && st == BSP_OK; ++r) st = plan_passes<float>(p, spec, p->fields, s, nullptr, split, part);
       if (st != BSP_OK) break;
       if ((ce = cudaEventRecord(e1, s)) != cudaSuccess || (ce = cudaEventSynchronize(e1)) != cudaSuccess) {
         st = cuda_fail(ce, "pass autotune timing");
@@ -741,13 +745,17 @@ bsp_status build_levels(bsp_plan* p, cudaStream_t s) {
         if (G.where[pi] < 0) return fail(BSP_ERR_CUDA, "internal: a pair of the contraction has no slot");
         tmap[i] = G.where[pi] * L.np + lc[i];
       }
-      const long long chunks = L.nvox() / kTcVoxelChunk;
+      // under a memory budget the level is contracted slab by slab over the slab's voxels
+      const long long cvox = p->slab_nx ? (long long)p->slab_len(p->n_slabs() - 1) * S * S : L.nvox();
+      const long long chunks = cvox / kTcVoxelChunk;
       long long gy = std::min<long long>(std::max(1, p->n_sm), chunks);
       L.vpb = ((chunks + gy - 1) / gy) * kTcVoxelChunk;
-      L.gridy = (int)((L.nvox() + L.vpb - 1) / L.vpb);
+      L.gridy = p->slab_nx ? (int)gy : (int)((L.nvox() + L.vpb - 1) / L.vpb);
       // partial sums sized for the largest split the autotuner may pick
       const long long gmax = p->autotune ? std::min<long long>((long long)kTuneMults[kNumTune - 1] * std::max(1, p->n_sm), chunks) : gy;
-      L.gridy_cap = (int)((L.nvox() + ((chunks + gmax - 1) / gmax) * kTcVoxelChunk - 1) / (((chunks + gmax - 1) / gmax) * kTcVoxelChunk));
+      L.gridy_cap = p->slab_nx ? L.gridy  // every slab runs L.gridy blocks
+                               : (int)((L.nvox() + ((chunks + gmax - 1) / gmax) * kTcVoxelChunk - 1) /
+                                       (((chunks + gmax - 1) / gmax) * kTcVoxelChunk));
       if ((st = dev_upload(p, G.slots, &L.d_tc_groups, s)) != BSP_OK) return st;
       L.tc_off = tmap;
       if ((st = dev_alloc(p, tc_partial_entries(std::max(L.n_tg, 1), std::max(L.kt, 1), std::max(L.gridy, L.gridy_cap), L.np) * sizeof(float2), &tmp)) != BSP_OK)
@@ -770,7 +778,13 @@ bsp_status build_levels(bsp_plan* p, cudaStream_t s) {
       if ((st = dev_upload(p, src, &L.d_shells, s)) != BSP_OK) return st;
       if ((st = dev_alloc(p, (size_t)nsh * (size_t)L.nvox() * re, &L.fields)) != BSP_OK) return st;
     }
-    if (p->prec == BSP_MIXED_BF16X3 && L.n_tg > 0) {
+    if (p->prec == BSP_MIXED_BF16X3 && L.n_tg > 0 && p->slab_nx) {
+      // one x-slab's split fields [2][ns][slab planes x S^2]: a full slab and the last one
+      st = encode_split_map(&L.tmap, p->fields, (long long)p->slab_len(0) * S * S, nsh, L.np);
+      if (st == BSP_OK)
+        st = encode_split_map(&L.tmap_last, p->fields, (long long)p->slab_len(p->n_slabs() - 1) * S * S, nsh, L.np);
+      if (st != BSP_OK) return st;
+    } else if (p->prec == BSP_MIXED_BF16X3 && L.n_tg > 0) {
       st = encode_split_map(&L.tmap, L.top ? p->fields : L.fields, L.nvox(), nsh, L.np);
       if (st != BSP_OK) return st;
     }
@@ -789,7 +803,7 @@ bsp_status build_levels(bsp_plan* p, cudaStream_t s) {
     }
     p->levels.push_back(std::move(L));
   }
-  if (p->prec == BSP_MIXED_BF16X3 && p->autotune) {
+  if (p->prec == BSP_MIXED_BF16X3 && p->autotune && !p->slab_nx) {
     if ((st = autotune_levels(p, s)) != BSP_OK) return st;
   }
   if (p->prec == BSP_MIXED_BF16X3) {

@@ -223,8 +223,9 @@ struct TcBin {
   int off;
   double scale;
 };
-// Every bin of every level in one launch (one warp per bin, a fixed summation order).
-bsp_status launch_reduce_tc_all(const TcBin* bins, int n, double* msum, cudaStream_t s);
+// Every bin of every level in one launch (one warp per bin, a fixed summation order); with
+// `accumulate` the sums are added to msum (the x-slabs of a budgeted plan).
+bsp_status launch_reduce_tc_all(const TcBin* bins, int n, double* msum, cudaStream_t s, bool accumulate = false);
 
 // ---------------------------------------------------------------- gradient (bispec_grad.cu)
 bsp_status launch_build_w(const double* g, const double* cnorm, const int* ptr, const int* idx, int n_entries,

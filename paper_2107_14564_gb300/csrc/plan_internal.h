@@ -53,7 +53,9 @@ struct ContractLevel {
   void* fields = nullptr;     // [shells][g^3] for lower levels (split planes [2][shells][g^3] for
                               // tensor-core plans)
   int* d_shells = nullptr;    // source field of each destination field of the level sampling
-  CUtensorMap tmap{};         // tensor-core plans: the level's split fields
+  CUtensorMap tmap{};         // tensor-core plans: the level's split fields (under a memory
+                              // budget: those of a full x-slab)
+  CUtensorMap tmap_last{};    // under a memory budget: the last (shorter) x-slab's split fields
   // CUDA-core contraction
   Tile* d_tiles = nullptr;
   int2* d_pairs = nullptr;

@@ -84,17 +84,17 @@ def _layout_picks(plan, extra):
     return sorted(picks)
 
 
-def _sampled(lib, ng, ns, top, n_index, f, seed, beta, prec, extra, budgets=(0,), layout=True):
-    """Condition-scaled and plain relative errors of the picked bins, one row per memory budget,
-    and the picks (each level and tile covered is asserted)."""
+def _sampled(lib, ng, ns, top, n_index, f, seed, beta, prec, extra, budgets=(0,), layout=True, variants=None):
+    """Condition-scaled and plain relative errors of the picked bins, one row per memory budget
+    (or per (precision, budget) in `variants`); with `layout`, every level and tile is covered."""
     edges = np.linspace(1.0, top, ns + 1)
     delta = fieldgen.quadratic_field(ng, float(ng), n_index, f, seed)
     spec = fieldgen.half_spectrum_c64(delta)
     del delta
     bs = []
     picks = None
-    for budget in budgets:
-        gp = lib.Plan(ng, float(ng), edges, 20, 20, rsd=beta is not None, beta=beta or 0.0, precision=prec,
+    for prec_v, budget in (variants or [(prec, b) for b in budgets]):
+        gp = lib.Plan(ng, float(ng), edges, 20, 20, rsd=beta is not None, beta=beta or 0.0, precision=prec_v,
                       mem_budget_bytes=budget)
         if budget:  # fields produced and reduced x-slab by x-slab; the plan holds less than all fields
             assert gp.slabs[1] > 1 and gp.device_bytes < gp.field_bytes
@@ -143,12 +143,13 @@ def test_ng256_fp32_sampled_bins(lib):
 
 
 def test_ng768_fp32_forward_sampled_bins(lib):
-    """The forward-only Ng=768 FP32 workload (24 shells k_f..192 k_f), with every field resident
-    (24 x 768^3 FP32 = 43.5 GB) and under an 8 GiB budget for shell fields (x-slabs of 151
-    planes, plan-time FP64 counts in slabs too); bins of the largest, a middle and the smallest
-    k1 shell against the oracle."""
-    cond, rel = _sampled(lib, 768, 24, 192.0, 1.5, 0.05, 7, None, "fp32", [-1, -2, 300, 0], budgets=(0, 8 << 30),
-                         layout=False)
+    """The forward-only Ng=768 workload (24 shells k_f..192 k_f): the FP32 plan with every field
+    resident (24 x 768^3 FP32 = 43.5 GB) and under an 8 GiB budget for shell fields (x-slabs of 151
+    planes, plan-time FP64 counts in slabs too), and the split-BF16 plan under the same budget
+    (split fields of one slab, one tensor-core level); bins of the largest, a middle and the
+    smallest k1 shell against the oracle."""
+    cond, rel = _sampled(lib, 768, 24, 192.0, 1.5, 0.05, 7, None, "fp32/mixed", [-1, -2, 300, 0], layout=False,
+                         variants=[("fp32", 0), ("fp32", 8 << 30), ("mixed_bf16x3", 8 << 30)])
     assert np.max(cond) < 1e-4, (cond, rel)
 
 

@@ -140,3 +140,67 @@ def test_adjoint_under_a_memory_budget(lib):
     assert np.abs(got - want).max() / np.abs(want).max() < 1e-4
     res = fbe.estimate(spec.cpu().numpy().astype(np.complex128), pl, beta=beta, with_abs=True)
     assert np.max(np.abs(b.cpu().numpy() - res["b"]) / res["b_scale"]) < 1e-4
+
+
+@pytest.mark.slow
+def test_config5_loss_gradient_finite_differences(lib):
+    """The differentiable workload at its size: Ng=256, 24 shells k_f..64 k_f, the quadratic field
+    with P = k^-1.5 and f = 0.05, loss L = sum_t (B_t - B_ana,t)^2 / B_ana,t^2 (B_ana of Eq. (3.2)
+    at the bins' shell means). dL/d delta from autograd (forward bsp_estimate of the FP32 plan,
+    backward the hand-written adjoint bsp_grad) against central differences of L at 64 seeded
+    voxels and along one seeded random direction, the differences taken with the FP64 GPU plan's
+    forward on delta +- h e (spectra shifted on the device by +- h e^{-i k.x_v}). L is a polynomial
+    of degree 6 in delta and h = 1e-3 of the field's r.m.s., so the differences' truncation error is
+    ~1e-6 relative; the FP32 gradient's own rounding dominates."""
+    from oracle import analytic as A
+    from paper_2107_14564_gb300.autograd import bispectrum
+    ng, ns = 256, 24
+    edges = P.linear_edges(ns, 1.0, 64.0)
+    delta64 = fieldgen.quadratic_field(ng, float(ng), 1.5, 0.05, 5)
+    delta = delta64.astype(np.float32)
+    gp = lib.Plan(ng, float(ng), edges, 20, 20, precision="fp32")
+    g64 = lib.Plan(ng, float(ng), edges, 20, 20, precision="fp64")
+    pl = P.make_plan(ng, float(ng), edges)
+    tr = gp.triplets
+    p = [A.power_law(pl.kf * tr[k], 1.5) for k in ("k1", "k2", "k3")]
+    bana = torch.from_numpy(A.b_ana(p[0], p[1], p[2], 0.05)).cuda()
+
+    d = torch.from_numpy(delta).cuda().requires_grad_(True)
+    b = bispectrum(d, gp)
+    loss = (((b - bana) / bana) ** 2).sum()
+    loss.backward()
+    grad = d.grad.double()
+    gp.check()
+
+    # FP64 forward on spectra of delta +- h e
+    spec0 = torch.from_numpy(np.fft.rfftn(delta.astype(np.float64))).cuda()
+    m = torch.fft.fftfreq(ng, d=1.0 / ng, dtype=torch.float64, device="cuda")
+    mz = torch.arange(ng // 2 + 1, dtype=torch.float64, device="cuda")
+
+    def loss64(spec):
+        bb, _ = g64.estimate(spec.contiguous(), with_grid=False)
+        return float((((bb - bana) / bana) ** 2).sum())
+
+    h = 1e-3 * float(delta.astype(np.float64).std())
+    vox = fieldgen.random_voxels(ng, 64, 6)
+    fd = np.empty(len(vox))
+    for i, v in enumerate(vox):
+        x, y, z = np.unravel_index(int(v), (ng, ng, ng))
+        ph = torch.exp(-2j * np.pi * (m[:, None, None] * x + m[None, :, None] * y + mz[None, None, :] * z) / ng)
+        fd[i] = (loss64(spec0 + h * ph) - loss64(spec0 - h * ph)) / (2 * h)
+    got = grad.reshape(-1)[torch.from_numpy(vox).cuda()].cpu().numpy()
+    gmax = float(grad.abs().max())
+    err = np.abs(got - fd)
+    print(f"\n[grad FD] 64 voxels: max |err| / |fd| {np.max(err / np.abs(fd)):.2e}, median {np.median(err / np.abs(fd)):.2e}; "
+          f"max |err| / max|grad| {err.max() / gmax:.2e}")
+    assert np.all(err <= 1e-3 * np.abs(fd) + 1e-4 * gmax), (err, fd)
+    # one random direction u: (L(delta + h u) - L(delta - h u)) / 2h = grad . u
+    u = fieldgen.random_weights(ng ** 3, 7).reshape(ng, ng, ng)
+    u /= np.sqrt((u * u).sum())
+    su = torch.from_numpy(np.fft.rfftn(u)).cuda()
+    hu = 1e-3 * float(np.sqrt((delta.astype(np.float64) ** 2).sum()))
+    fdu = (loss64(spec0 + hu * su) - loss64(spec0 - hu * su)) / (2 * hu)
+    gu = float((grad.cpu().numpy() * u).sum())
+    print(f"[grad FD] direction: fd {fdu:.6e} grad.u {gu:.6e} rel {abs(gu - fdu) / abs(fdu):.2e}")
+    assert abs(gu - fdu) <= 1e-3 * abs(fdu)
+    g64.check()

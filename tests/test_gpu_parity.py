@@ -386,3 +386,32 @@ def test_memory_budget_slabs(lib, prec):
         assert np.max(_cond_err(b, res)) < 1e-4
         assert np.max(np.abs(b - b0) / res["b_scale"]) < 1e-5
     assert np.array_equal(np.isnan(g), np.isnan(res["grid"]))
+
+
+def test_mixed_memory_budget_slabs(lib):
+    """A split-BF16 plan under a budget of 40 x-planes of shell fields (Ng = 128, evaluation grid
+    128^3, 12 shells: slabs of 40 planes, the last 8): the Z pass writes each slab's split fields,
+    the tensor-core contraction reads them through a full-slab or a last-slab tensor map and adds
+    the slabs' sums. Against the oracle and the plan that holds every field, with and without the
+    autotuner (whose Z-pass timing then runs on the first slab only)."""
+    ng = 128
+    edges = _edges(ng, 12)
+    spec = _spec(ng, 1.5, 0.05, 29, c64=True)
+    pl, res = _oracle(spec, ng, edges, with_abs=True)
+    full = lib.Plan(ng, float(ng), edges, precision="mixed_bf16x3")
+    size = full.ng_eval
+    assert size == 128
+    b0, _ = full.estimate(torch.from_numpy(spec).cuda())
+    b0 = b0.cpu().numpy()
+    for tune in (False, True):
+        gp = lib.Plan(ng, float(ng), edges, precision="mixed_bf16x3", autotune=tune,
+                      mem_budget_bytes=40 * 12 * size * size * 4)
+        assert gp.slabs == (40, 4)
+        assert gp.device_bytes < full.device_bytes
+        b, g = gp.estimate(torch.from_numpy(spec).cuda())
+        gp.check()
+        b, g = b.cpu().numpy(), g.cpu().numpy()
+        assert np.max(_cond_err(b, res)) < 1e-4
+        assert np.max(np.abs(b - b0) / res["b_scale"]) < 1e-5
+        assert np.array_equal(np.isnan(g), np.isnan(res["grid"]))
+        gp.close()
