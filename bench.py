@@ -170,20 +170,25 @@ def oracle_sample(w, spec_c64, n_triplets, n_pairs):
     t1 = time.perf_counter()
     t_fft = (t1 - t0) / 2
     a, b = w["ns"] - 1, w["ns"] - 2
+    # the oracle's per-pair steps (fbe.triple_sums): the pair product, a stacked copy of the third
+    # fields the pair needs, one matrix-vector product; timed here with two third fields
+    # as many third fields as an average pair has (the stacked copy's size drives its cost)
+    m = max(1, round(n_triplets / n_pairs))
     t1 = time.perf_counter()
     prod = (f[a] * f[b]).ravel()
     t2 = time.perf_counter()
-    mat = np.stack([f[a].ravel(), f[b].ravel()])
+    mat = np.stack([f[a].ravel() if i % 2 == 0 else f[b].ravel() for i in range(m)])
     t3 = time.perf_counter()
-    for _ in range(4):
-        mat @ prod
+    mat @ prod
     t4 = time.perf_counter()
+    del mat
     t_pair = t2 - t1
-    t_dot = (t4 - t3) / 8
-    total = w["ns"] * t_fft + n_pairs * t_pair + n_triplets * t_dot
-    desc = (f"oracle timed on 2 of {w['ns']} shell FFTs, 1 of {n_pairs} pair products and 8 of "
-            f"{n_triplets} triple-product sums at full Ng={w['ng']}, extrapolated to one estimate "
-            f"({total:.1f} s)")
+    t_third = (t3 - t2 + t4 - t3) / m  # per third field: its copy and its dot product
+    total = w["ns"] * t_fft + n_pairs * t_pair + n_triplets * t_third
+    desc = (f"oracle timed on 2 of {w['ns']} shell FFTs and one pair's product, copied {m} third fields and "
+            f"dot products ({n_pairs} pairs, {n_triplets} bins) at full Ng={w['ng']}, extrapolated to one "
+            f"estimate ({total:.1f} s); a lower bound: checked against full timed estimates at Ng=256 "
+            f"(bench.py --validate-oracle-model) it came out 40-50% short")
     return n_triplets / total, t4 - t0, desc
 
 
@@ -197,9 +202,9 @@ def run_reference(args, w):
     spec = make_input(w, w["seed"])
     pl = P.make_plan(w["ng"], w["box"], edges_of(w), w["n_mu"], w["n_t"])
     # bin list from the data-independent counts (plan time, excluded as in the GPU arm)
-    n_trip, n_pairs = gpu_free_bin_counts(pl)
+    n_trip, n_pairs = oracle_bin_counts(pl)
     for _ in range(args.warmup):
-        pass
+        oracle_sample(w, spec, n_trip, n_pairs)
     vals = []
     t_all = time.perf_counter()
     for _ in range(args.steps):
@@ -210,7 +215,9 @@ def run_reference(args, w):
     cores = os.cpu_count()
     line = {"impl": "reference", "metric": metric_name(w), "value": value, "unit": "bins/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1000.0 * elapsed / max(args.steps, 1), "higher_is_better": True,
+            # one step is one (extrapolated) oracle estimate; the timed samples took sample_ms each
+            "ms_per_step": 1000.0 * n_trip / value, "sample_ms": 1000.0 * elapsed / max(args.steps, 1),
+            "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_of(w, "fp64"),
             "cpu_baseline": {"value": value, "unit": "bins/s", "cores": cores, "kind": "oracle",
@@ -219,11 +226,37 @@ def run_reference(args, w):
     print(json.dumps(line), flush=True)
 
 
-def gpu_free_bin_counts(pl):
-    """(kept bins, distinct pairs) from the oracle's own counting fields at this size is too slow
-    for a bench step; the counts come from the CUDA plan when it exists, else from the triangle
-    inequality (an upper bound), which is what the reference arm uses."""
+def validate_oracle_model(args):
+    """Check the cpu_baseline extrapolation against a full timed oracle estimate (workload
+    --workload, Ng=256 by default; the counting fields, plan time in both arms, are computed first
+    and not timed). Prints one JSON line with the predicted and the measured seconds."""
+    import numpy as np
+    from oracle import fbe
     from oracle import plan as P
+    w = WORKLOADS["ng256" if args.workload == "ng512_rsd" and not args.full_size_oracle else args.workload]
+    spec = make_input(w, w["seed"])
+    pl = P.make_plan(w["ng"], w["box"], edges_of(w), w["n_mu"], w["n_t"])
+    n_trip, n_pairs = oracle_bin_counts(pl)
+    oracle_sample(w, spec, n_trip, n_pairs)  # warm-up
+    preds = [n_trip / oracle_sample(w, spec, n_trip, n_pairs)[0] for _ in range(3)]
+    if args.full_size_oracle:  # the bins' counts only divide: skip the (untimed) counting pass
+        counts = (list(pl.candidates), np.ones(n_trip), np.ones(n_trip))
+    else:
+        counts = fbe.kept_triplets(pl)
+    assert len(counts[0]) == n_trip
+    t0 = time.perf_counter()
+    fbe.estimate(spec.astype(np.complex128), pl, beta=w["beta"], counts=counts)
+    full = time.perf_counter() - t0
+    pred = statistics.median(preds)
+    print(json.dumps({"oracle_model_check": f"ng{w['ng']}", "bins": n_trip, "bins_per_s": round(n_trip / full, 3), "predicted_s": round(pred, 2), "measured_s": round(full, 2),
+                      "model_error": round(pred / full - 1.0, 3), "cores": os.cpu_count()}), flush=True)
+
+
+def oracle_bin_counts(pl):
+    """(bins, distinct pairs (a, b)) of the oracle's candidate list: the bins whose shell edges
+    allow a closed triangle. Counting the closed triangles themselves (N_tri > 0) takes the
+    oracle's counting-field FFTs, too slow for a bench step; for the bench workloads the candidate
+    list equals the kept bins (3624 at Ng=512 and 1654 at Ng=256, the CUDA plans' counts)."""
     trips = pl.candidates
     pairs = {(a, b) for a, b, _ in trips}
     return len(trips), len(pairs)
@@ -573,7 +606,15 @@ def main():
                     help="GiB of shell fields a plan may hold (0: all); FP32/FP64 plans then stream x-slabs")
     ap.add_argument("--no-autotune", action="store_true",
                     help="plans skip the contraction autotuner (fixed split: one voxel block per SM)")
+    ap.add_argument("--validate-oracle-model", action="store_true",
+                    help="compare the cpu_baseline extrapolation with a full timed oracle estimate (Ng=256 unless "
+                         "--full-size-oracle)")
+    ap.add_argument("--full-size-oracle", action="store_true",
+                    help="with --validate-oracle-model: time the full oracle estimate of the bench workload itself")
     args = ap.parse_args()
+    if args.validate_oracle_model:
+        validate_oracle_model(args)
+        return
     if args.warmup < 3:
         log("[bench] warmup raised to 3")
         args.warmup = 3

@@ -31,7 +31,7 @@
 //     the B stage for the loader and (NA chunks later) the A stage for the generators. One
 //     issuing thread reaches an N = 64 MMA every ~45 cycles, about half the tensor core's rate;
 //     several issuers keep it fed.
-//   Every RUN chunks (4096 voxels) the generators read the accumulators back (tcgen05.ld) into
+//   Every RUN chunks (8192 voxels) the generators read the accumulators back (tcgen05.ld) into
 //   compensated FP32 sums (FP64 arithmetic runs at a small fraction of the FP32 rate on this GPU)
 //   and signal the MMA warps, whose next MMAs restart the accumulators, so FP32 sums stay short.
 // Blocks keep their sums as compensated FP32 pairs; a second kernel adds them in FP64 in a fixed
@@ -51,7 +51,7 @@ constexpr int kTcGenWarps = 16;                     // generator warps, then the
 template <int KT>
 constexpr int tc_threads() { return (kTcGenWarps + 1 + KT) * 32; }
 constexpr int kTcChunk = kTcVoxelChunk;             // voxels per chunk (K of one stage; one TMA box)
-constexpr int kTcRun = 64;                          // chunks per FP32 accumulation run (4096 voxels)
+constexpr int kTcRun = 128;                         // chunks per FP32 accumulation run (8192 voxels)
 constexpr uint32_t kTcCols = 512;                   // TMEM columns (one block per SM)
 constexpr long long kWaitLimit = 1LL << 22;         // mbarrier polls before giving up
 static_assert(kTcChunk == 64, "one 128-byte TMA box row per chunk");

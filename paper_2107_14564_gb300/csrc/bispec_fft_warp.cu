@@ -292,8 +292,13 @@ __global__ void __launch_bounds__(XY<N>::kThreads, XPASS ? 4 : 3) xy_warp_kernel
 // ---------------------------------------------------------------- Z pass
 // SLAB: only the x-slab of a.slab_x0 / a.slab_nx, fields [n][x - slab_x0][y][z] (FP32, or split
 // planes when a.split_lo != 0).
+// Register budget: 4 blocks per SM (64 registers) unless the line is long (768, 1024: 24-32
+// points per lane spill below 128 registers).
+template <int S>
+__host__ __device__ constexpr int z_min_blocks() { return S >= 768 ? 2 : 4; }
+
 template <int S, bool SLAB>
-__global__ void __launch_bounds__(kZThreads, 4) z_warp_kernel(PassArgs a, long long n_lines) {
+__global__ void __launch_bounds__(kZThreads, z_min_blocks<S>()) z_warp_kernel(PassArgs a, long long n_lines) {
   constexpr int M = S / 2;
   constexpr int LPL = Radices<M>::lpl;
   constexpr int LPW = 32 / LPL;  // lines per warp at a time
