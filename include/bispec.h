@@ -88,11 +88,13 @@ typedef struct {
                               time (the largest slab within the budget, sums added in FP64), on one
                               contraction level. The X/Y pass buffers are outside the budget. A
                               budget below one x-plane of all shells is BSP_ERR_INVALID_ARG;
-                              BSP_MIXED_BF16X3 plans whose fields exceed it are
-                              BSP_ERR_NOT_SUPPORTED. Results equal the unbudgeted plan's up to the
-                              order of the sums. */
+                              BSP_MIXED_BF16X3 plans whose fields exceed it need an evaluation grid
+                              of 128..1024 points of the form 2^p or 3*2^p (else
+                              BSP_ERR_NOT_SUPPORTED) and then hold one slab of split fields, so
+                              bsp_contract refuses them. Results equal the unbudgeted plan's up to
+                              the order of the sums. */
   int autotune;            /* 1: at creation, time the tensor-core contraction of every level with
-                              its voxels split over 1, 2 and 4 x (SM count) blocks per M tile and
+                              its voxels split over 1, 2 and 4 x (SM count) blocks per tile group and
                               keep the fastest (BSP_MIXED_BF16X3 plans; the split changes only the
                               order of the FP64 cross-block sums), and time the persistent Y and Z
                               FFT passes with grids of 1 .. 16 x (SM count) blocks and keep the
@@ -286,8 +288,9 @@ BSP_API bsp_status bsp_timing_read(bsp_plan* plan, double* ms, int* n_calls, lon
  * device memory (reads of the non-zero inputs it needs plus its outputs, each once) and
  * flops[s] of its arithmetic core (0 where it is negligible): for the contraction, one product
  * per pair and one multiply-add per bin and voxel on CUDA cores, or 3 x 2 x pairs x padded shell
- * columns x voxels for the split-BF16 tensor-core GEMM, summed over the contraction levels.
- * Host-side, no GPU work. */
+ * columns x voxels for the split-BF16 tensor-core GEMM, each pair counted on its smallest exact
+ * contraction level (a split-BF16 plan may contract a pair on a larger level where that is
+ * faster; the extra work is not counted). Host-side, no GPU work. */
 BSP_API bsp_status bsp_plan_stage_work(const bsp_plan* plan, double* bytes, double* flops);
 
 /* Bytes bsp_estimate_host copies host->device per call (the spectrum box of the outermost shell). */

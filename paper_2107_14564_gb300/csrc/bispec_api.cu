@@ -372,21 +372,33 @@ void stage_work(const bsp_plan* p, double* bytes, double* flops) {
     bytes[BSP_STAGE_YPASS] += ce * ng * (double)xlines + ce * ng * ng * r;
     bytes[BSP_STAGE_ZPASS] += ce * ng * ng * r + re * ng * ng * ng;
   }
-  // contraction levels: fields read once per level (lower levels also read their samples of the
-  // evaluation grid and write them), work per level on its g^3 grid
-  for (const ContractLevel& L : p->levels) {
-    const double nv = (double)L.nvox();
-    const double nsh = (double)L.shells.size();
-    long long npairs = 0;
-    for (size_t i = 0; i < L.bins.size(); ++i) {
-      const bsp_triplet& a = p->trips[L.bins[i]];
-      if (i == 0 || a.a != p->trips[L.bins[i - 1]].a || a.b != p->trips[L.bins[i - 1]].b) npairs += 1;
+  // contraction levels, each pair on its smallest exact grid (a split-BF16 plan may contract some
+  // pairs on a larger level where that is faster; that extra work is not counted): fields read
+  // once per level (lower levels also read their samples of the evaluation grid and write them),
+  // work per level on its g^3 grid
+  for (const auto& lv : p->exact_levels) {
+    const int g = lv.first;
+    const std::vector<int>& bins = lv.second;
+    const bool top = g == p->ngs;
+    const double nv = p->dim == 2 ? (double)g * g : (double)g * g * g;
+    int nsh = 0;
+    if (top) {
+      nsh = p->ns + p->n_extra();
+    } else {
+      std::vector<char> used(p->ns, 0);
+      for (int b : bins) used[p->trips[b].a] = used[p->trips[b].b] = used[p->trips[b].c] = 1;
+      for (char u : used) nsh += u;
     }
-    bytes[BSP_STAGE_CONTRACT] += re * nsh * nv * (L.top ? 1.0 : 3.0);
-    if (p->prec == BSP_MIXED_BF16X3)
-      flops[BSP_STAGE_CONTRACT] += 3.0 * 2.0 * (double)npairs * (double)L.np * nv;  // split-BF16 GEMM
+    long long npairs = 0;
+    for (size_t i = 0; i < bins.size(); ++i) {
+      const bsp_triplet& a = p->trips[bins[i]];
+      if (i == 0 || a.a != p->trips[bins[i - 1]].a || a.b != p->trips[bins[i - 1]].b) npairs += 1;
+    }
+    bytes[BSP_STAGE_CONTRACT] += re * nsh * nv * (top ? 1.0 : 3.0);
+    if (p->prec == BSP_MIXED_BF16X3)  // split-BF16 GEMM over the padded shell columns
+      flops[BSP_STAGE_CONTRACT] += 3.0 * 2.0 * (double)npairs * (double)tc_padded_shells(nsh) * nv;
     else
-      flops[BSP_STAGE_CONTRACT] += ((double)npairs + 2.0 * (double)L.bins.size()) * nv;
+      flops[BSP_STAGE_CONTRACT] += ((double)npairs + 2.0 * (double)bins.size()) * nv;
   }
   bytes[BSP_STAGE_FINALIZE] = 8.0 * (double)p->trips.size() * 3 + 8.0 * p->n_cells();
 }

@@ -566,8 +566,8 @@ long long g2_elems(const bsp_plan* p) {
 }
 
 // Contraction autotuner (plans created with autotune = 1): for every tensor-core level, time its
-// kernel on the plan's own buffers with the voxel range of each M tile split over m x (SM count)
-// blocks, m in kTuneMults (fewer when the level has fewer 128-voxel chunks), 3 launches after one
+// kernel on the plan's own buffers with the voxel range of each tile group split over m x (SM
+// count) blocks, m in kTuneMults (fewer when the level has fewer 64-voxel chunks), 3 launches after one
 // warm-up each, and keep the fastest split. More blocks than SMs trade partial sums and block
 // start-up for a shorter tail. The values computed are the same for every split up to the
 // order of the FP64 cross-block sums.
@@ -668,9 +668,79 @@ bsp_status autotune_passes(bsp_plan* p, cudaStream_t s) {
   return st;
 }
 
+// Cost model of one tensor-core contraction level, in microseconds on the whole GPU: every
+// tile group of the level costs, per 64-voxel chunk on one SM, kTcChunkCycles[KT - 1] cycles
+// (NP = 32 padded shells; twice that at NP = 64) whatever number of its 64 slots hold pairs;
+// a level also costs a fixed launch, pipeline fill and flush time, and a level below the
+// evaluation grid the Z pass's writes of its split fields (4 bytes per shell and voxel). The
+// per-chunk cycles are measured per-SM times of levels with one tile group of KT = 1 (900-935
+// cycles on 192^3 .. 768^3 grids) and KT = 3 (1133-1174 cycles on 384^3 and 768^3) on a GB300 at
+// 2070 MHz, KT = 2 between them. The level-field writes are charged at half the copy bandwidth:
+// an Ng = 768 Z pass writing 7.5 GB of level fields beside 43.5 GB of evaluation-grid fields took
+// 19.7 ms, the same fields written x-slab by x-slab without them 14.9 ms.
+namespace {
+constexpr double kTcChunkCycles[3] = {925.0, 1040.0, 1150.0};
+constexpr double kTcLevelFixedUs = 4.0;
+constexpr double kTcSmMhz = 2070.0;
+constexpr double kTcFieldBytesPerUs = 3.4e6;
+
+double tc_level_cost_us(const bsp_plan* p, int g, const std::vector<int>& bins) {
+  const bool top = g == p->ngs;
+  std::vector<int> loc(p->ns, -1);
+  int nsh = 0;
+  if (top) {
+    for (int n = 0; n < p->ns; ++n) loc[n] = nsh++;
+  } else {
+    std::vector<char> used(p->ns, 0);
+    for (int b : bins) used[p->trips[b].a] = used[p->trips[b].b] = used[p->trips[b].c] = 1;
+    for (int n = 0; n < p->ns; ++n)
+      if (used[n]) loc[n] = nsh++;
+  }
+  std::vector<int2> pairs;
+  for (size_t i = 0; i < bins.size(); ++i) {
+    const bsp_triplet& t = p->trips[bins[i]];
+    if (i == 0 || t.a != p->trips[bins[i - 1]].a || t.b != p->trips[bins[i - 1]].b)
+      pairs.push_back(make_int2(loc[t.a], loc[t.b]));
+  }
+  const int np = tc_padded_shells(nsh);
+  const TcGrouping G = group_pairs(pairs, nsh, np == 32 ? 3 : 2);
+  const double vox = (double)g * g * g;
+  const double chunks_per_sm = std::ceil(vox / kTcVoxelChunk / std::max(1, p->n_sm));
+  const double cyc = kTcChunkCycles[std::min(std::max(G.kt, 1), 3) - 1] * (np / 32.0);
+  double us = kTcLevelFixedUs + chunks_per_sm * G.n_tg * cyc / kTcSmMhz;
+  if (!top) us += (double)nsh * vox * 4.0 / kTcFieldBytesPerUs;
+  return us;
+}
+}  // namespace
+
+// Merging of tensor-core contraction levels: a level whose pairs fit into the spare slots (or a
+// larger KT) of the next level up can cost less there than on its own smaller grid, because a
+// level's time follows its tile groups, not its pairs. Levels are merged bottom-up, each into
+// the next level, while the model above says the sum of the two costs more than the merged
+// level. A pair's evaluation grid stays exact on any larger divisor grid, so a merge changes
+// only the order of the additions in a bin's sum.
+void merge_tc_levels(const bsp_plan* p, std::vector<std::pair<int, std::vector<int>>>& by_g) {
+  size_t i = 0;
+  while (i + 1 < by_g.size()) {
+    std::vector<int> u = by_g[i].second;
+    u.insert(u.end(), by_g[i + 1].second.begin(), by_g[i + 1].second.end());
+    std::sort(u.begin(), u.end());
+    const double apart = tc_level_cost_us(p, by_g[i].first, by_g[i].second) +
+                         tc_level_cost_us(p, by_g[i + 1].first, by_g[i + 1].second);
+    const double merged = tc_level_cost_us(p, by_g[i + 1].first, u);
+    if (merged < apart) {
+      by_g[i + 1].second.swap(u);
+      by_g.erase(by_g.begin() + (long)i);
+    } else {
+      ++i;
+    }
+  }
+}
+
 // Contraction levels (see ContractLevel): each pair (a, b) of the kept bins goes to the smallest
 // divisor g of the evaluation grid (g % 8 == 0, g >= 16) above r_a + r_b + r_cmax - 3, the largest
-// wavevector component of its triple products.
+// wavevector component of its triple products; split-BF16 plans then merge levels where the
+// cost model above favours it.
 bsp_status build_levels(bsp_plan* p, cudaStream_t s) {
   const int S = p->ngs;
   std::vector<std::pair<int, std::vector<int>>> by_g;  // ascending g
@@ -697,6 +767,8 @@ bsp_status build_levels(bsp_plan* p, cudaStream_t s) {
     t = u;
   }
   std::sort(by_g.begin(), by_g.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
+  p->exact_levels = by_g;
+  if (p->prec == BSP_MIXED_BF16X3) merge_tc_levels(p, by_g);
   const size_t re = p->elem();
   bsp_status st;
   std::vector<ZLevel> zl;  // levels the split Z pass writes

@@ -129,6 +129,9 @@ struct bsp_plan {
   int nwxi = 0, nwyi = 0;
   int rmax = 0;
   std::vector<ContractLevel> levels;
+  // each level's side and bins before split-BF16 plans merge levels (every pair on its smallest
+  // exact grid): the algorithm's work, which bsp_plan_stage_work counts
+  std::vector<std::pair<int, std::vector<int>>> exact_levels;
   int* d_error = nullptr;
   // gradient resources (built by the first bsp_grad call)
   bool grad_ready = false;

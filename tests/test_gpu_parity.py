@@ -238,6 +238,31 @@ def test_autotuned_plan_matches(lib):
     assert torch.equal(a.shell_fields(d), b.shell_fields(d))
 
 
+def test_mixed_levels_merge_only_upwards(lib):
+    """Split-BF16 plans merge a contraction level into the next one up where the level's pairs
+    cost less in that level's tile groups. Every bin must then sit on a grid at least as fine as
+    the smallest exact one (the FP32 plan's level of the same bin), no level may be empty, and the
+    estimate stays within the bound."""
+    ng = 128
+    edges = _edges(ng, 20, 32.0)
+    spec = _spec(ng, 1.5, 0.05, 22, c64=True)
+    pl, res = _oracle(spec, ng, edges, with_abs=True)
+    m = lib.Plan(ng, float(ng), edges, precision="mixed_bf16x3")
+    f = lib.Plan(ng, float(ng), edges, precision="fp32")
+    side_m = np.array([g for g, _ in m.tuning])[m.bin_level]
+    side_f = np.array([g for g, _ in f.tuning])[f.bin_level]
+    assert np.all(side_m >= side_f)
+    assert np.all(m.ng_eval % side_m == 0)
+    assert set(m.bin_level) == set(range(len(m.tuning)))
+    assert len(m.tuning) <= len(f.tuning)
+    b = m.estimate(torch.from_numpy(spec).cuda())[0].cpu().numpy()
+    m.check()
+    assert np.max(_cond_err(b, res)) < 1e-4
+    print(f"\nlevels FP32 {[g for g, _ in f.tuning]} split BF16 {[g for g, _ in m.tuning]}")
+    m.close()
+    f.close()
+
+
 def test_host_entry_reads_only_the_shell_box(lib):
     """bsp_estimate_host copies only |m_x|, |m_y|, m_z < r of the outermost shell: NaN written
     everywhere else in the host spectrum changes nothing."""
