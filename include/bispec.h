@@ -263,6 +263,13 @@ BSP_API bsp_status bsp_last_sums(const bsp_plan* plan, const double** msum);
  * calls made after this one. */
 BSP_API bsp_status bsp_plan_check(bsp_plan* plan, void* stream);
 
+/* Self-test of the failure path above (no counterpart in the paper): enqueue on `stream` one warp
+ * that waits, through the tensor-core contraction's bounded mbarrier wait capped at 4096 polls,
+ * on a barrier nothing arrives at; the wait runs out and raises this plan's failure flag, so the
+ * next bsp_plan_check returns BSP_ERR_TIMEOUT (once). Nothing else is in flight in that kernel:
+ * the context stays usable. Errors: BSP_ERR_INVALID_ARG (NULL plan), BSP_ERR_CUDA (launch). */
+BSP_API bsp_status bsp_selftest_wait_timeout(bsp_plan* plan, void* stream);
+
 /* Stages of one bsp_estimate, in launch order (for bsp_timing_read and bsp_plan_stage_work). */
 enum {
   BSP_STAGE_XPASS = 0,    /* shell-masked C2C along x (Eq. (2.8)) */

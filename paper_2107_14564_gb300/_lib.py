@@ -70,6 +70,7 @@ SIGNATURES = {
     "bsp_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "bsp_last_sums": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p)]),
     "bsp_plan_check": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "bsp_selftest_wait_timeout": (C.c_int, [C.c_void_p, C.c_void_p]),
     "bsp_timing_enable": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "bsp_timing_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int),
                                   C.POINTER(C.c_longlong)]),

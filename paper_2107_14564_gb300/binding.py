@@ -146,6 +146,10 @@ def bsp_plan_check(handle, stream=None) -> None:
     check(_lib.load().bsp_plan_check(handle, C.c_void_p(_stream_ptr(stream))))
 
 
+def bsp_selftest_wait_timeout(handle, stream=None) -> None:
+    check(_lib.load().bsp_selftest_wait_timeout(handle, C.c_void_p(_stream_ptr(stream))))
+
+
 def bsp_version() -> str:
     return _lib.load().bsp_version().decode()
 
@@ -333,4 +337,4 @@ class Plan:
 
 __all__ = ["Plan", "BispecError", "bsp_plan_create", "bsp_plan_destroy", "bsp_plan_info",
            "bsp_plan_triplets", "bsp_plan_grid", "bsp_plan_tuning", "bsp_plan_bin_levels", "bsp_plan_host_input_bytes", "bsp_plan_slabs", "bsp_plan_pass_tuning", "bsp_shell_fields", "bsp_contract", "bsp_estimate",
-           "bsp_estimate_host", "bsp_estimate_batched", "Batch", "bsp_spectrum", "bsp_grad", "bsp_last_sums", "bsp_plan_check", "bsp_version", "TRIPLET_DTYPE"]
+           "bsp_estimate_host", "bsp_estimate_batched", "Batch", "bsp_spectrum", "bsp_grad", "bsp_last_sums", "bsp_plan_check", "bsp_selftest_wait_timeout", "bsp_version", "TRIPLET_DTYPE"]

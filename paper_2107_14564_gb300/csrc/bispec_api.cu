@@ -547,6 +547,11 @@ bsp_status bsp_plan_check(bsp_plan* p, void* stream) {
   return BSP_OK;
 }
 
+bsp_status bsp_selftest_wait_timeout(bsp_plan* p, void* stream) {
+  if (!p) return fail(BSP_ERR_INVALID_ARG, "plan is NULL");
+  return launch_wait_selftest(p->d_error, static_cast<cudaStream_t>(stream));
+}
+
 bsp_status bsp_estimate(bsp_plan* p, const void* spec, double* b_triplet, double* b_grid, void* stream) {
   if (!p || !spec || !b_triplet) return fail(BSP_ERR_INVALID_ARG, "NULL argument");
   cudaStream_t s = static_cast<cudaStream_t>(stream);

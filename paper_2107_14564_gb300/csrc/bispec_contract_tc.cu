@@ -77,9 +77,10 @@ struct TcLayout {
   static_assert(kBPlane % 1024 == 0, "boxes stay 1024-byte aligned");
 };
 
-// Poll an mbarrier; give up after kWaitLimit polls or when another warp aborted.
+// Poll an mbarrier; give up after Limit polls or when another warp aborted.
+template <long long Limit = kWaitLimit>
 __device__ __forceinline__ bool tc_wait1(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
-  for (long long i = 0; i < kWaitLimit; ++i) {
+  for (long long i = 0; i < Limit; ++i) {
     if (ptx::mbar_try_wait(bar, parity)) return true;
     if ((i & 255) == 255 && *abort_flag) return false;
   }
@@ -87,8 +88,27 @@ __device__ __forceinline__ bool tc_wait1(uint64_t* bar, uint32_t parity, volatil
 }
 // The same for a whole warp, with a warp-uniform result: every lane calls it, and a warp leaves its
 // loop as one, so its warp-collective tcgen05 instructions are never run by part of a warp.
+template <long long Limit = kWaitLimit>
 __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
-  return __all_sync(0xffffffffu, tc_wait1(bar, parity, abort_flag));
+  return __all_sync(0xffffffffu, tc_wait1<Limit>(bar, parity, abort_flag));
+}
+
+// Self-test of the give-up path (no counterpart in the paper): one warp waits, with the loop
+// above capped at kSelftestPolls polls, on an mbarrier that nothing arrives at, and raises the
+// error flag as a contraction block does when a wait runs out. Nothing else is in flight: no
+// copies, no tensor memory.
+constexpr long long kSelftestPolls = 4096;
+__global__ void tc_wait_selftest_kernel(int* error) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    ptx::mbar_init(&bar, 1);
+    ptx::fence_mbar_init();
+    abort_flag = 0;
+  }
+  __syncthreads();
+  const bool done = tc_wait<kSelftestPolls>(&bar, 0u, &abort_flag);
+  if (!done && threadIdx.x == 0) atomicExch(error, 1);
 }
 
 // FP32 sum kept as an unevaluated pair s + c (the rounding error of every addition goes into c),
@@ -429,6 +449,12 @@ bsp_status launch_reduce_tc_all(const TcBin* bins, int n, double* msum, cudaStre
 }
 
 int tc_padded_shells(int ns) { return ns <= 32 ? 32 : 64; }
+
+bsp_status launch_wait_selftest(int* error, cudaStream_t s) {
+  tc_wait_selftest_kernel<<<1, 32, 0, s>>>(error);
+  BSP_CUDA(cudaGetLastError());
+  return BSP_OK;
+}
 
 size_t tc_partial_entries(int n_tg, int kt, int gridy, int np) {
   return (size_t)gridy * n_tg * kt * kTcSlots * np;

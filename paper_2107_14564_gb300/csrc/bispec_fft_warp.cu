@@ -162,22 +162,30 @@ template <int N> struct XY {
   static constexpr int kThreads = kLines * kLpl;
 };
 
-// Block b takes items b, b + gridDim.x, ... The Y pass runs persistent blocks: the input tile of
-// the next item is fetched with cp.async (zero-filled outside the shell) into the second of two
-// tile buffers while the current item is transformed, so its global-load latency is hidden. The
-// X pass, whose tiles lie mostly outside the shell (few loads), runs one item per block with
-// plain loads (more resident blocks, one tile buffer).
+// Persistent blocks: block b takes items b, b + gridDim.x, ... The input tile of the next item is
+// fetched with cp.async (zero-filled outside the shell) into the second of two tile buffers while
+// the current item is transformed, so its global-load latency is hidden; the X pass applies the
+// Kaiser factor when it reads the tile (counting fields, which have no spectrum, are stored
+// directly). The line buffers of the transform overlay the current item's tile once every line
+// has read it, so a block holds two regions of max(tile, line buffers) and four blocks fit an SM
+// at length 384.
+template <int N> __host__ __device__ constexpr int xy_region(int rmax) {
+  return 2 * rmax * kTileLd > kLines * line_ld<N>() ? 2 * rmax * kTileLd : kLines * line_ld<N>();
+}
+// Register budget: as many blocks per SM as the shared memory admits at the longest lines of
+// each length (4 up to 384 points, 3 at 512, 2 beyond), so long lines keep their points in
+// registers instead of spilling for blocks that could not be resident anyway.
+template <int N> __host__ __device__ constexpr int xy_min_blocks() { return N <= 384 ? 4 : N <= 512 ? 3 : 2; }
 template <int N, bool XPASS>
-__global__ void __launch_bounds__(XY<N>::kThreads, XPASS ? 4 : 3) xy_warp_kernel(PassArgs a, int n_items) {
+__global__ void __launch_bounds__(XY<N>::kThreads, xy_min_blocks<N>()) xy_warp_kernel(PassArgs a, int n_items) {
   constexpr int LPL = XY<N>::kLpl;
   constexpr int NT = XY<N>::kThreads;
   constexpr int E = N / LPL;
   constexpr int kBufLd = line_ld<N>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* tw = reinterpret_cast<float2*>(smem_raw);  // N entries exp(2 pi i t / N)
-  float2* bufs = tw + N;                               // kLines x kBufLd
-  float2* tiles = bufs + (size_t)kLines * kBufLd;      // 2 x (2 rmax) x kTileLd
-  const int tile_elems = 2 * a.rmax * kTileLd;
+  const int region = xy_region<N>(a.rmax);  // two regions: a tile, or once it is read, the line buffers
+  float2* tiles = tw + N;
   const int tid = threadIdx.x;
   for (int i = tid; i < N; i += NT) tw[i] = static_cast<const float2*>(a.stw)[i];
   // ---- input tile [row = k + r - 1][line] of an item: issue the copies (one commit group)
@@ -198,18 +206,14 @@ __global__ void __launch_bounds__(XY<N>::kThreads, XPASS ? 4 : 3) xy_warp_kernel
         const int mx = row - (r - 1);
         const int kz = it.v0 + l;
         const int q = mx * mx + ky * ky + kz * kz;
-        // one item per block (nothing to overlap): plain loads, shell mask and Kaiser factor
-        float2 val = make_float2(0.f, 0.f);
-        if (l < it.cnt && q >= g.qlo && q < g.qhi) {
+        const bool in = l < it.cnt && q >= g.qlo && q < g.qhi;
+        if (spec) {
           const int ix = mx < 0 ? mx + ng : mx;
-          val = spec ? spec[((long long)ix * ng + iy) * hz + kz] : make_float2(1.f, 0.f);
-          if (a.rsd) {
-            const float fac = (float)(1.0 + a.beta * (double)(kz * kz) / (double)q);
-            val.x *= fac;
-            val.y *= fac;
-          }
+          const float2* src = in ? spec + ((long long)ix * ng + iy) * hz + kz : spec;
+          ptx::cp_async8_zfill(tile + row * kTileLd + l, src, in ? 8u : 0u);
+        } else {
+          tile[row * kTileLd + l] = in ? make_float2(1.f, 0.f) : make_float2(0.f, 0.f);
         }
-        tile[row * kTileLd + l] = val;
       }
     } else {
       const float2* g1 = static_cast<const float2*>(a.g1) + g.g1_off;
@@ -228,13 +232,15 @@ __global__ void __launch_bounds__(XY<N>::kThreads, XPASS ? 4 : 3) xy_warp_kernel
   };
   int k = 0;
   if (blockIdx.x < n_items) issue(blockIdx.x, tiles);
-  // the X pass: exactly one item per block (gridDim.x == n_items), no loop
-  const int stride = XPASS ? n_items : (int)gridDim.x;
+  const int stride = (int)gridDim.x;
   for (int item = blockIdx.x; item < n_items; item += stride, ++k) {
-    float2* tile = tiles + (size_t)(k & 1) * tile_elems;
+    float2* tile = tiles + (size_t)(k & 1) * region;
+    float2* bufs = tile;
     const int next = item + stride;
-    if (!XPASS && next < n_items) {
-      issue(next, tiles + (size_t)((k + 1) & 1) * tile_elems);
+    if (next < n_items) {
+      // the next tile goes where the previous item's line buffers were read out
+      if (k > 0) __syncthreads();
+      issue(next, tiles + (size_t)((k + 1) & 1) * region);
       ptx::cp_async_wait<1>();  // this item's copies (issued one iteration earlier) have landed
     } else {
       ptx::cp_async_wait<0>();
@@ -258,8 +264,19 @@ __global__ void __launch_bounds__(XY<N>::kThreads, XPASS ? 4 : 3) xy_warp_kernel
           const int pos = lane + b * LPL + rr * (N / R1);
           const int kk = pos < N / 2 ? pos : pos - N;
           const int row = kk + r - 1;
-          v[b * R1 + rr] = (row >= 0 && row < w) ? tile[row * kTileLd + l] : make_float2(0.f, 0.f);
+          float2 t = (row >= 0 && row < w) ? tile[row * kTileLd + l] : make_float2(0.f, 0.f);
+          if (XPASS && a.rsd) {  // Kaiser factor (Eq. (3.4)) of the shell's modes, in FP32
+            const int kz = it.v0 + l;
+            const int q = kk * kk + it.u * it.u + kz * kz;
+            if (row >= 0 && row < w && l < it.cnt && q >= g.qlo && q < g.qhi) {
+              const float fac = 1.0f + (float)a.beta * ((float)(kz * kz) / (float)q);
+              t.x *= fac;
+              t.y *= fac;
+            }
+          }
+          v[b * R1 + rr] = t;
         }
+      __syncthreads();  // every line has read the tile its buffers overlay
       float2* buf = bufs + (size_t)l * kBufLd;
       warp_fft_from<N, LPL, 0, 1>(v, buf, lane, tw);
       constexpr int RL = last_radix<N>();
@@ -606,18 +623,14 @@ bsp_status launch_zf(const PassArgs& a, const float* gfield, long long n_lines, 
 template <int N, bool XPASS>
 bsp_status launch_xy(const PassArgs& a, int n_items, int n_sm, cudaStream_t s) {
   if (n_items == 0) return BSP_OK;
-  // tiles of 2 r - 1 rows of the largest shell: two for persistent blocks, one otherwise
-  const int ntiles = XPASS ? 1 : 2;
-  const size_t smem =
-      ((size_t)N + (size_t)kLines * line_ld<N>() + (size_t)ntiles * (2 * a.rmax) * kTileLd) * sizeof(float2);
+  // two regions, each holding a tile of 2 r - 1 rows of the largest shell or, once it is read,
+  // the line buffers
+  const size_t smem = ((size_t)N + 2 * (size_t)xy_region<N>(a.rmax)) * sizeof(float2);
   BSP_CUDA(cudaFuncSetAttribute(xy_warp_kernel<N, XPASS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  long long blocks = n_items;
-  if (!XPASS) {
-    int per_sm = 0;
-    BSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, xy_warp_kernel<N, XPASS>, XY<N>::kThreads, smem));
-    blocks = std::min<long long>((long long)std::max(per_sm, 1) * std::max(n_sm, 1), n_items);
-    if (a.grid_blocks > 0) blocks = std::min<long long>(a.grid_blocks, n_items);
-  }
+  int per_sm = 0;
+  BSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, xy_warp_kernel<N, XPASS>, XY<N>::kThreads, smem));
+  long long blocks = std::min<long long>((long long)std::max(per_sm, 1) * std::max(n_sm, 1), n_items);
+  if (!XPASS && a.grid_blocks > 0) blocks = std::min<long long>(a.grid_blocks, n_items);
   xy_warp_kernel<N, XPASS><<<(unsigned)blocks, XY<N>::kThreads, smem, s>>>(a, n_items);
   BSP_CUDA(cudaGetLastError());
   return BSP_OK;

@@ -209,6 +209,8 @@ struct TcArgs {
   int* error;               // set to 1 when a bounded wait gives up
 };
 int tc_padded_shells(int ns);
+// One warp whose bounded wait on an mbarrier nothing arrives at runs out and sets *error.
+bsp_status launch_wait_selftest(int* error, cudaStream_t s);
 size_t tc_partial_entries(int n_tg, int kt, int gridy, int np);
 bsp_status launch_contract_tc(const TcArgs& a, const CUtensorMap* tmap, cudaStream_t s);
 // Encode the tensor map of split fields at `base` ([2][rows][nvox] bf16) for NP-row boxes.

@@ -145,6 +145,30 @@ def test_fp32_parity_ragged(lib, prec):
     assert np.array_equal(np.isnan(g.cpu().numpy()), np.isnan(res["grid"]))
 
 
+@pytest.mark.parametrize("prec", ["fp32", "mixed_bf16x3"])
+def test_rsd_parity_on_the_warp_passes(lib, prec):
+    """Kaiser RSD (Eq. (3.4), beta = 0.5) through the warp FFT passes, whose X pass applies the
+    factor in FP32 as it reads each tile: Ng = 192 with 12 shells up to 48 k_f (a 192^3
+    evaluation grid), shell fields and the estimate against the oracle."""
+    ng = 192
+    edges = P.linear_edges(12, 1.0, 48.0)
+    spec = _spec(ng, 1.5, 0.05, 24, c64=True)
+    pl, res = _oracle(spec, ng, edges, beta=0.5, with_abs=True)
+    gp = lib.Plan(ng, float(ng), edges, rsd=True, beta=0.5, precision=prec)
+    assert gp.ng_eval >= 128  # the warp passes
+    d = torch.from_numpy(spec).cuda()
+    b = gp.estimate(d)[0].cpu().numpy()
+    gp.check()
+    assert np.max(_cond_err(b, res)) < (1e-6 if prec == "fp32" else 1e-4)
+    if prec == "fp32":
+        spec64 = spec.astype(np.complex128) * fbe.kaiser_factor_half(ng, 0.5)
+        want = fbe.shell_fields_on_grid(spec64, pl, gp.ng_eval)
+        got = gp.shell_fields(d).cpu().numpy()
+        for n in range(pl.ns):
+            assert np.abs(got[n] - want[n]).max() <= 2e-6 * np.abs(want[n]).max(), n
+    gp.close()
+
+
 def test_contract_on_oracle_fields(lib):
     """The contraction alone, fed the oracle's FP64 fields sampled on the plan's evaluation grid;
     its sums must equal the oracle's sums over the full Ng^3 grid (the coarser grid is exact)."""
@@ -261,6 +285,26 @@ def test_mixed_levels_merge_only_upwards(lib):
     print(f"\nlevels FP32 {[g for g, _ in f.tuning]} split BF16 {[g for g, _ in m.tuning]}")
     m.close()
     f.close()
+
+
+def test_bounded_wait_running_out_is_reported(lib):
+    """The device-side failure path: a bounded mbarrier wait that runs out (the self-test kernel
+    waits on a barrier nothing arrives at) raises the plan's flag; bsp_plan_check reports
+    BSP_ERR_TIMEOUT once and clears it, and the plan's next estimate is still correct."""
+    ng = 64
+    edges = _edges(ng, 8)
+    spec = _spec(ng, 1.5, 0.05, 23, c64=True)
+    pl, res = _oracle(spec, ng, edges, with_abs=True)
+    gp = lib.Plan(ng, float(ng), edges, precision="mixed_bf16x3")
+    gp.check()
+    lib.bsp_selftest_wait_timeout(gp.handle)
+    with pytest.raises(RuntimeError, match="BSP_ERR_TIMEOUT"):
+        gp.check()
+    gp.check()  # reported once
+    b = gp.estimate(torch.from_numpy(spec).cuda())[0].cpu().numpy()
+    gp.check()
+    assert np.max(_cond_err(b, res)) < 1e-4
+    gp.close()
 
 
 def test_host_entry_reads_only_the_shell_box(lib):
