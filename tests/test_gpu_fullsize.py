@@ -124,7 +124,8 @@ def _sampled(lib, ng, ns, top, n_index, f, seed, beta, prec, extra, budgets=(0,)
     cond = np.abs(got - want) / scale
     rel = np.abs(got - want) / np.abs(want)
     cancel = scale / np.abs(want)  # how far each bin's sum cancels below its terms
-    print(f"\n[{prec} Ng={ng}] {len(picks)} bins: condition-scaled max {cond.max():.2e} median {np.median(cond):.2e}; "
+    print(f"\n[{prec} Ng={ng}] condition-scaled max per plan: {', '.join(f'{c:.2e}' for c in cond.max(axis=1))}")
+    print(f"[{prec} Ng={ng}] {len(picks)} bins: condition-scaled max {cond.max():.2e} median {np.median(cond):.2e}; "
           f"relative max {rel.max():.2e} median {np.median(rel):.2e}; relative max over bins cancelling < 1e3: "
           f"{rel[:, cancel < 1e3].max() if np.any(cancel < 1e3) else float('nan'):.2e}")
     return cond, rel
@@ -134,12 +135,12 @@ def test_ng512_rsd_mixed_sampled_bins(lib):
     # the layout picks plus bins of the largest k1 shell (equilateral, squeezed, linear), a mid
     # shell and the lowest
     cond, rel = _sampled(lib, 512, 32, 128.0, 1.5, 0.05, 4, 0.5, "mixed_bf16x3", [-1, -2, -17, 1500, 0, 7])
-    assert np.max(cond) < 1e-4, (cond, rel)
+    assert np.max(cond) < 2e-6, (cond, rel)  # the stated split-BF16 bound
 
 
 def test_ng256_fp32_sampled_bins(lib):
     cond, rel = _sampled(lib, 256, 24, 64.0, 1.5, 0.05, 3, None, "fp32", [-1, -3, -40, 600, 0, 11])
-    assert np.max(cond) < 1e-4, (cond, rel)
+    assert np.max(cond) < 1e-7, (cond, rel)  # the stated FP32 bound
 
 
 def test_ng768_fp32_forward_sampled_bins(lib):
@@ -150,12 +151,13 @@ def test_ng768_fp32_forward_sampled_bins(lib):
     smallest k1 shell against the oracle."""
     cond, rel = _sampled(lib, 768, 24, 192.0, 1.5, 0.05, 7, None, "fp32/mixed", [-1, -2, 300, 0], layout=False,
                          variants=[("fp32", 0), ("fp32", 8 << 30), ("mixed_bf16x3", 8 << 30)])
-    assert np.max(cond) < 1e-4, (cond, rel)
+    assert np.max(cond) < 1e-6, (cond, rel)
 
 
 def test_ng256_all_bins_fp32_and_mixed(lib):
     """Every bin of the Ng=256 workload (24 shells, 20x20 cells) against the full FP64 oracle
-    estimate, for the FP32 and the split-BF16 plans: the condition-scaled error of every bin, and
+    estimate, for the FP32 and the split-BF16 plans: the condition-scaled error of every bin (the
+    stated bounds, 1e-7 and 2e-6), and
     the plain relative error of the bins whose sums cancel to no less than 1e-3 (FP32) or 1e-2
     (split BF16) of their terms. Plain relative error = condition-scaled error x cancellation ratio,
     so each bin class inherits its bound from the condition-scaled one."""
@@ -166,7 +168,7 @@ def test_ng256_all_bins_fp32_and_mixed(lib):
     res = fbe.estimate(spec.astype(np.complex128), pl, with_abs=True)
     want, scale = res["b"], res["b_scale"]
     cancel = scale / np.abs(want)
-    for prec, bound, cmax in (("fp32", 1e-5, 1e3), ("mixed_bf16x3", 1e-5, 1e2)):
+    for prec, bound, cmax in (("fp32", 1e-7, 1e3), ("mixed_bf16x3", 2e-6, 1e2)):
         gp = lib.Plan(ng, float(ng), edges, 20, 20, precision=prec)
         got = gp.estimate(torch.from_numpy(spec).cuda(), with_grid=False)[0].cpu().numpy()
         gp.check()
