@@ -476,7 +476,7 @@ def run_batch(args, w):
     import numpy as np
     import torch
     import fieldgen
-    from paper_2107_14564_gb300 import binding
+    from paper_2107_14564_gb300 import _lib, binding
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     plans, specs, nbytes = [], [], 0
     for ng, count in w["grids"]:
@@ -488,6 +488,21 @@ def run_batch(args, w):
             plans.append(plan)
             specs.append(torch.from_numpy(sp).cuda())
     bins = sum(p.n_triplets for p in plans)
+    # kernels per estimate of each plan, counted by the library on one timed estimate
+    import ctypes as C
+    lib = _lib.load()
+    per_plan = {}
+    for p, sp in zip(plans, specs):
+        if id(p) in per_plan:
+            continue
+        _lib.check(lib.bsp_timing_enable(p.handle, 1, 1))
+        p.estimate(sp, with_grid=False)
+        st_ms = (C.c_double * 5)()
+        ncalls, nl = C.c_int(), C.c_longlong()
+        _lib.check(lib.bsp_timing_read(p.handle, st_ms, C.byref(ncalls), C.byref(nl)))
+        _lib.check(lib.bsp_timing_enable(p.handle, 0, 0))
+        per_plan[id(p)] = int(nl.value) // max(1, int(ncalls.value))
+    launches = sum(per_plan[id(p)] for p in plans)
     batch = binding.Batch(plans, specs)
     for _ in range(args.warmup):
         batch.run()
@@ -519,7 +534,7 @@ def run_batch(args, w):
             "config": {"workload": w["text"], "precision": args.precision, "fields": len(specs),
                        "l2": "inputs larger than L2 (%.1f GB of spectra)" % (nbytes / 1e9)},
             "n_bins": bins, "fields_per_sec": sum(p.n_shells for p in plans) / (ms / 1000.0),
-            "ms_without_graph": ms_loop, "gpu_launches": 6 * len(specs), "clocks": clk,
+            "ms_without_graph": ms_loop, "gpu_launches": launches * args.steps, "clocks": clk,
             "roofline": None, "cpu_baseline": None, "e2e": None}
     print(json.dumps(line), flush=True)
     batch.close()

@@ -5,12 +5,14 @@
 // M[(a,b), c] = sum_x (d_a d_b)(x) d_c(x): a tile owns up to 4 pairs (a, b) and 4 consecutive
 // c, i.e. 16 outputs held in registers by one thread. A block walks a contiguous voxel range in
 // chunks staged in shared memory (all shells of the chunk), so every field value read from
-// HBM serves every tile of the block. FP32 plans accumulate in FP32 over kFlushChunks chunks
+// HBM serves every tile of the block; the next chunk is copied in with cp.async into a second
+// buffer while the current one is used. FP32 plans accumulate in FP32 over kFlushChunks chunks
 // and then add into FP64; FP64 plans accumulate in FP64. Blocks write FP64 partial sums,
 // which a second kernel adds in a fixed order (deterministic results).
 #include <algorithm>
 
 #include "common.cuh"
+#include "tc_ptx.cuh"
 
 namespace bsp {
 
@@ -22,8 +24,9 @@ template <typename T>
 __global__ void __launch_bounds__(kContractThreads)
 contract_simt_kernel(ContractArgs a, long long vox_per_block) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* dsm = reinterpret_cast<T*>(smem_raw);   // [ns][kChunk + 1]
+  T* dsm0 = reinterpret_cast<T*>(smem_raw);  // two chunks [ns][kChunk + 1]
   constexpr int LD = kChunk + 1;
+  const int chunk_elems = a.ns * LD;
   const T* fields = static_cast<const T*>(a.fields);
   const int tile = blockIdx.y * kContractThreads + threadIdx.x;
   const bool active = tile < a.ntiles;
@@ -52,14 +55,27 @@ contract_simt_kernel(ContractArgs a, long long vox_per_block) {
 
   const long long v_begin = (long long)blockIdx.x * vox_per_block;
   const long long v_end = min(v_begin + vox_per_block, a.nvox);
-  int run = 0;
-  for (long long vb = v_begin; vb < v_end; vb += kChunk) {
-    __syncthreads();
+  // copy the chunk at vb into dst (zeros past v_end), one commit group
+  auto stage = [&](long long vb, T* dst) {
     for (int i = threadIdx.x; i < a.ns * kChunk; i += kContractThreads) {
       const int n = i / kChunk;
       const int v = i - n * kChunk;
       const long long gv = vb + v;
-      dsm[n * LD + v] = gv < v_end ? fields[(long long)n * a.nvox + gv] : T(0);
+      const bool in = gv < v_end;
+      ptx::cp_async_zfill<(int)sizeof(T)>(dst + n * LD + v, in ? fields + (long long)n * a.nvox + gv : fields,
+                                          in ? (uint32_t)sizeof(T) : 0u);
+    }
+    ptx::cp_async_commit();
+  };
+  if (v_begin < v_end) stage(v_begin, dsm0);
+  int run = 0, k = 0;
+  for (long long vb = v_begin; vb < v_end; vb += kChunk, ++k) {
+    const T* dsm = dsm0 + (size_t)(k & 1) * chunk_elems;
+    if (vb + kChunk < v_end) {
+      stage(vb + kChunk, dsm0 + (size_t)((k + 1) & 1) * chunk_elems);
+      ptx::cp_async_wait<1>();  // this chunk's copies (issued one iteration earlier) have landed
+    } else {
+      ptx::cp_async_wait<0>();
     }
     __syncthreads();
     if (active) {
@@ -78,27 +94,34 @@ contract_simt_kernel(ContractArgs a, long long vox_per_block) {
       if (++run == kFlushChunks) {
         run = 0;
 #pragma unroll
-        for (int k = 0; k < 16; ++k) { acc64[k] += (double)acc[k]; acc[k] = T(0); }
+        for (int q = 0; q < 16; ++q) { acc64[q] += (double)acc[q]; acc[q] = T(0); }
       }
     }
+    __syncthreads();  // every thread is done with this buffer before the next copy into it
   }
-  if (active) {
-    double* out = a.partial + ((long long)blockIdx.x * a.ntiles + tile) * 16;
+  if (active) {  // partial[(tile * 16 + k) * gridx + block]: an output's block sums are contiguous
+    double* out = a.partial + (long long)tile * 16 * a.gridx + blockIdx.x;
 #pragma unroll
-    for (int k = 0; k < 16; ++k) out[k] = acc64[k] + (double)acc[k];
+    for (int k = 0; k < 16; ++k) out[(long long)k * a.gridx] = acc64[k] + (double)acc[k];
   }
 }
 
-// msum[map[tile][k]] = scale * sum over blocks of partial[block][tile][k], blocks in order
+// msum[map[tile][k]] = scale * sum over blocks of partial[tile][k][block], in a fixed order
 // (added to msum when accumulating x-slabs).
+// One warp per (tile, entry): lane l adds the block sums b = l, l + 32, ... (contiguous loads
+// across the warp), then the lanes' sums are added by a fixed shuffle tree.
 __global__ void reduce_partials_kernel(ContractArgs a) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= a.ntiles * 16) return;
+  const int idx = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (idx >= a.ntiles * 16) return;  // warp-uniform
   const int dst = a.tile_map[idx];
-  if (dst < 0) return;
+  if (dst < 0) return;  // warp-uniform
+  const double* src = a.partial + (long long)idx * a.gridx;
   double s = 0.0;
-  for (int b = 0; b < a.gridx; ++b) s += a.partial[(long long)b * a.ntiles * 16 + idx];
-  a.msum[dst] = a.accumulate ? a.msum[dst] + a.scale * s : a.scale * s;
+  for (int b = lane; b < a.gridx; b += 32) s += src[b];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  if (lane == 0) a.msum[dst] = a.accumulate ? a.msum[dst] + a.scale * s : a.scale * s;
 }
 
 template <typename T>
@@ -108,7 +131,7 @@ bsp_status launch_contract_simt(const ContractArgs& a, cudaStream_t s) {
   const long long per_block_chunks = (chunks + a.gridx - 1) / a.gridx;
   const long long vpb = per_block_chunks * kChunk;
   dim3 grid(a.gridx, (a.ntiles + kContractThreads - 1) / kContractThreads);
-  const size_t smem = (size_t)a.ns * (kChunk + 1) * sizeof(T);
+  const size_t smem = 2 * (size_t)a.ns * (kChunk + 1) * sizeof(T);
   BSP_CUDA(cudaFuncSetAttribute(contract_simt_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem));
   contract_simt_kernel<T><<<grid, kContractThreads, smem, s>>>(a, vpb);
@@ -117,9 +140,9 @@ bsp_status launch_contract_simt(const ContractArgs& a, cudaStream_t s) {
 }
 
 bsp_status launch_reduce_partials(const ContractArgs& a, cudaStream_t s) {
-  const int n = a.ntiles * 16;
+  const long long n = (long long)a.ntiles * 16 * 32;  // one warp per entry
   if (n == 0) return BSP_OK;
-  reduce_partials_kernel<<<(n + 255) / 256, 256, 0, s>>>(a);
+  reduce_partials_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a);
   BSP_CUDA(cudaGetLastError());
   return BSP_OK;
 }

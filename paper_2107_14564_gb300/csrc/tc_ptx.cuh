@@ -48,6 +48,13 @@ __device__ __forceinline__ void cp_async8_zfill(void* smem_dst, const void* gmem
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(smem_dst)), "l"(gmem_src), "r"(src_bytes)
                : "memory");
 }
+// B-byte (4, 8 or 16) asynchronous copy through L1; src_bytes = 0 writes zeros and reads nothing.
+template <int B>
+__device__ __forceinline__ void cp_async_zfill(void* smem_dst, const void* gmem_src, uint32_t src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(smem_u32(smem_dst)), "l"(gmem_src), "n"(B),
+               "r"(src_bytes)
+               : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }

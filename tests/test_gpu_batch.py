@@ -63,3 +63,31 @@ def test_batch_against_oracle(setup):
         res = fbe.estimate(sp.astype(np.complex128), pl, with_abs=True)
         b = p.estimate(s, with_grid=False)[0].cpu().numpy()
         assert np.max(np.abs(b - res["b"]) / res["b_scale"]) < 1e-4
+
+
+@pytest.mark.slow
+def test_batch64_graph_equals_single_estimates(setup):
+    """The 64-field workload at its full size (16 fields at Ng = 128, 24 at 192, 24 at 256, 16
+    shells each, split-BF16 plans): one captured-graph replay of all 64 estimates gives, field by
+    field, exactly the bins of the single estimates, twice."""
+    lib = setup[0]
+    plans, specs = [], []
+    by_ng = {}
+    for ng, count in ((128, 16), (192, 24), (256, 24)):
+        by_ng[ng] = lib.Plan(ng, float(ng), P.linear_edges(16, 1.0, ng / 4), 10, 10, precision="mixed_bf16x3")
+        for i in range(count):
+            sp = fieldgen.half_spectrum_c64(fieldgen.quadratic_field(ng, float(ng), 1.5, 0.05, 1000 + len(specs)))
+            plans.append(by_ng[ng])
+            specs.append(torch.from_numpy(sp).cuda())
+    ref = [p.estimate(s, with_grid=False)[0].clone() for p, s in zip(plans, specs)]
+    batch = lib.Batch(plans, specs)
+    for _ in range(2):
+        outs = batch.run()
+        torch.cuda.synchronize()
+        assert len(outs) == 64
+        for r, o in zip(ref, outs):
+            assert torch.equal(r, o)
+    batch.close()
+    for p in by_ng.values():
+        p.check()
+        p.close()
