@@ -20,12 +20,22 @@ constexpr int kChunk = 64;         // voxels per shared-memory chunk
 constexpr int kContractThreads = 256;
 constexpr int kFlushChunks = 16;   // FP32 run length: 1024 voxels
 
+// Two neighbouring voxels of one field, read from shared memory in one 8-byte (FP32) or
+// 16-byte (FP64) load.
+template <typename T> struct Pair2;
+template <> struct Pair2<float> { using type = float2; };
+template <> struct Pair2<double> { using type = double2; };
+// Row stride of a staged chunk: even, so voxel pairs are aligned; 66 words puts field n's pair
+// (v, v + 1) on the bank pair (n + v / 2) mod 16.
+constexpr int kChunkLd = kChunk + 2;
+
 template <typename T>
 __global__ void __launch_bounds__(kContractThreads)
 contract_simt_kernel(ContractArgs a, long long vox_per_block) {
+  using T2 = typename Pair2<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* dsm0 = reinterpret_cast<T*>(smem_raw);  // two chunks [ns][kChunk + 1]
-  constexpr int LD = kChunk + 1;
+  T* dsm0 = reinterpret_cast<T*>(smem_raw);  // two chunks [ns][kChunkLd]
+  constexpr int LD = kChunkLd;
   const int chunk_elems = a.ns * LD;
   const T* fields = static_cast<const T*>(a.fields);
   const int tile = blockIdx.y * kContractThreads + threadIdx.x;
@@ -79,17 +89,25 @@ contract_simt_kernel(ContractArgs a, long long vox_per_block) {
     }
     __syncthreads();
     if (active) {
-#pragma unroll 4
-      for (int v = 0; v < kChunk; ++v) {
-        T p[4], d[4];
+#pragma unroll 2
+      for (int v = 0; v < kChunk; v += 2) {  // voxels v and v + 1, added in that order
+        T2 p[4], d[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) p[i] = dsm[ia[i] * LD + v] * dsm[ib[i] * LD + v];
+        for (int i = 0; i < 4; ++i) {
+          const T2 x = *reinterpret_cast<const T2*>(dsm + ia[i] * LD + v);
+          const T2 y = *reinterpret_cast<const T2*>(dsm + ib[i] * LD + v);
+          p[i].x = x.x * y.x;
+          p[i].y = x.y * y.y;
+        }
 #pragma unroll
-        for (int j = 0; j < 4; ++j) d[j] = dsm[ic[j] * LD + v];
+        for (int j = 0; j < 4; ++j) d[j] = *reinterpret_cast<const T2*>(dsm + ic[j] * LD + v);
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i * 4 + j] = fma(p[i], d[j], acc[i * 4 + j]);
+          for (int j = 0; j < 4; ++j) {
+            acc[i * 4 + j] = fma(p[i].x, d[j].x, acc[i * 4 + j]);
+            acc[i * 4 + j] = fma(p[i].y, d[j].y, acc[i * 4 + j]);
+          }
       }
       if (++run == kFlushChunks) {
         run = 0;
@@ -131,7 +149,7 @@ bsp_status launch_contract_simt(const ContractArgs& a, cudaStream_t s) {
   const long long per_block_chunks = (chunks + a.gridx - 1) / a.gridx;
   const long long vpb = per_block_chunks * kChunk;
   dim3 grid(a.gridx, (a.ntiles + kContractThreads - 1) / kContractThreads);
-  const size_t smem = 2 * (size_t)a.ns * (kChunk + 1) * sizeof(T);
+  const size_t smem = 2 * (size_t)a.ns * kChunkLd * sizeof(T);
   BSP_CUDA(cudaFuncSetAttribute(contract_simt_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem));
   contract_simt_kernel<T><<<grid, kContractThreads, smem, s>>>(a, vpb);
