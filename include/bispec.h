@@ -152,9 +152,10 @@ BSP_API bsp_status bsp_plan_info(const bsp_plan* plan, int* n_triplets, int* n_s
                          size_t* field_bytes, size_t* device_bytes);
 
 /* The contraction levels of a plan (no counterpart in the paper): for level l < *n_levels
- * (ascending side), level_side[l] = its grid side g and blocks_mult[l] = the voxel blocks per M
- * tile divided by the SM count (the autotuner's choice; 1 without it; 0 for a level on the CUDA
- * cores). Arrays: host, at least max_levels entries each, may be NULL. */
+ * (ascending side), level_side[l] = its grid side g and blocks_mult[l] = the voxel blocks per
+ * tensor-core tile group divided by the SM count (the autotuner's choice; 1 without it; 0 for a
+ * level on the CUDA cores). Split-BF16 plans may have merged levels (a pair on a larger grid than
+ * its smallest exact one). Arrays: host, at least max_levels entries each, may be NULL. */
 BSP_API bsp_status bsp_plan_tuning(const bsp_plan* plan, int* n_levels, int* level_side, int* blocks_mult,
                                    int max_levels);
 

@@ -74,7 +74,7 @@ def bsp_plan_host_input_bytes(handle) -> int:
 
 
 def bsp_plan_tuning(handle):
-    """[(level side g, blocks per M tile / SM count)] in ascending g."""
+    """[(level side g, voxel blocks per tile group / SM count)] in ascending g."""
     n = C.c_int(0)
     check(_lib.load().bsp_plan_tuning(handle, C.byref(n), None, None, 0))
     side = (C.c_int * max(n.value, 1))()

@@ -68,7 +68,7 @@ struct ContractLevel {
   int4* d_tc_groups = nullptr;  // [n_tg * kTcSlots] slot fields and flags (see TcArgs)
   std::vector<int> tc_off;    // partial-sum entry of each of the level's bins
   int gridy_cap = 0;          // voxel blocks the partial-sum buffer holds
-  int tune_mult = 1;          // blocks per M tile / SM count chosen by the autotuner (1 without it)
+  int tune_mult = 1;          // voxel blocks per tile group / SM count chosen by the autotuner (1 without it)
   float2* tc_partial = nullptr;
   int dim = 3;                // 2: a level of a 2D plan (g^2 points)
   long long nvox() const { return dim == 2 ? (long long)g * g : (long long)g * g * g; }
