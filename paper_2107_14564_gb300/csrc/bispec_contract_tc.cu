@@ -201,11 +201,12 @@ __global__ void __launch_bounds__(tc_threads<KT>(), 1)
     constexpr uint32_t idesc = ptx::idesc_bf16_f32(128, L::kDN);
     const uint64_t bdesc0 = ptx::smem_desc_sw128(ptx::smem_u32(bs), 1024u);
     const uint32_t dcol = tmem + (uint32_t)(L::kAcc + L::kDN * j);
+    int sa = 0;          // i % kNA, kept as a counter (kNA need not be a power of two)
+    uint32_t pa = 0;     // (i / kNA) & 1
     for (int i = 0; i < nchunks; ++i) {
-      const int sa = i % L::kNA;
       const int sb = i % L::kNB;
       const bool first = (i % kTcRun) == 0;
-      if (!tc_wait(&gen[sa], (uint32_t)((i / L::kNA) & 1), abort_flag) ||
+      if (!tc_wait(&gen[sa], pa, abort_flag) ||
           !tc_wait(&full[sb], (uint32_t)((i / L::kNB) & 1), abort_flag) ||
           (first && i > 0 && !tc_wait(flushed, (uint32_t)((i / kTcRun - 1) & 1), abort_flag))) {
         failed = true;
@@ -222,6 +223,7 @@ __global__ void __launch_bounds__(tc_threads<KT>(), 1)
         ptx::mma_commit(&mmad[sb]);
       }
       __syncwarp();
+      if (++sa == L::kNA) { sa = 0; pa ^= 1u; }
     }
     if (lane == 0) ptx::mma_commit(drain);  // arrives once every MMA issued above is complete
     __syncwarp();
@@ -304,8 +306,8 @@ __global__ void __launch_bounds__(tc_threads<KT>(), 1)
       __syncwarp();
       if (lane == 0) ptx::mbar_arrive(&gen[s]);
     };
+    int sa = 0, sa_prev = L::kNA - 1;  // i % kNA and (i - 1) % kNA, kept as counters
     for (int i = 0; i < nchunks; ++i) {
-      const int sa = i % L::kNA;
       const int sb = i % L::kNB;
       if (!tc_wait(&full[sb], (uint32_t)((i / L::kNB) & 1), abort_flag)) {
         *abort_flag = 1;
@@ -325,7 +327,7 @@ __global__ void __launch_bounds__(tc_threads<KT>(), 1)
           }
       }
       // the previous chunk's A stores have landed while the loads were in flight: hand it over
-      if (i > 0) publish((i - 1) % L::kNA);
+      if (i > 0) publish(sa_prev);
       // A operand: the slot's KT pair products; tile 0 (f0, s ? f1 : f0), 1 (f0, f2), 2 (f1, f2)
       uint32_t pv[KT][8];
       if (warp_active) {
@@ -370,6 +372,8 @@ __global__ void __launch_bounds__(tc_threads<KT>(), 1)
         for (int j = 0; j < KT; ++j)
           ptx::tmem_st_16x256b_x2(tmem + lane_base + (uint32_t)(L::kAStage * sa + 32 * j + 16 * kg), pv[j]);
       }
+      sa_prev = sa;
+      if (++sa == L::kNA) sa = 0;
     }
     if (!failed && nchunks > 0) publish((nchunks - 1) % L::kNA);
     if (!failed && nchunks > 0) {
