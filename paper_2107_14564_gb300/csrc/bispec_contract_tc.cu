@@ -80,7 +80,9 @@ struct TcLayout {
 // Poll an mbarrier; give up after Limit polls or when another warp aborted.
 template <long long Limit = kWaitLimit>
 __device__ __forceinline__ bool tc_wait1(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
-  for (long long i = 0; i < Limit; ++i) {
+  static_assert(Limit > 0 && Limit < (1ll << 31), "poll count fits an int");
+  if (ptx::mbar_try_wait(bar, parity)) return true;  // the usual case: already complete
+  for (int i = 1; i < (int)Limit; ++i) {
     if (ptx::mbar_try_wait(bar, parity)) return true;
     if ((i & 255) == 255 && *abort_flag) return false;
   }
