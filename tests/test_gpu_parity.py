@@ -190,10 +190,11 @@ def test_host_entry_point(lib):
     spec = _spec(ng, 2.0, 0.1, 1, c64=True)
     gp = lib.Plan(ng, float(ng), edges, precision="fp32")
     b_dev, g_dev = gp.estimate(torch.from_numpy(spec).cuda())
-    pinned = torch.from_numpy(spec).pin_memory()
-    b_h, g_h = gp.estimate_host(pinned)
-    assert np.array_equal(b_h, b_dev.cpu().numpy())
-    assert np.array_equal(np.nan_to_num(g_h, nan=-1.0), np.nan_to_num(g_dev.cpu().numpy(), nan=-1.0))
+    # pinned and pageable host memory
+    for host in (torch.from_numpy(spec).pin_memory(), np.ascontiguousarray(spec)):
+        b_h, g_h = gp.estimate_host(host)
+        assert np.array_equal(b_h, b_dev.cpu().numpy())
+        assert np.array_equal(np.nan_to_num(g_h, nan=-1.0), np.nan_to_num(g_dev.cpu().numpy(), nan=-1.0))
 
 
 def test_errors_are_reported(lib):
